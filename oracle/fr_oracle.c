@@ -1,0 +1,386 @@
+/*
+ * fr_oracle.c -- plain, slow, obviously-correct CPU oracle for flow routing.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The product
+ * (GPU) path never links, imports or calls it, and shares no code with it.
+ *
+ * What it computes (Bangerth, "Massively parallel flow routing and drainage
+ * area determination"):
+ *   - local flow routing (Sec. 2.1 and its footnote; App. A): each cell gives
+ *     its water to the steepest lower neighbour (D8), or splits it among all
+ *     lower neighbours (MFD, App. A, with Freeman-style weights);
+ *   - global flow routing by the sequential high-to-low algorithm (Sec. 2.1,
+ *     Eq. high-to-low-procedure and the "global flow routing" listing): sort
+ *     cells high to low, start with w = r, pass each cell's water to its
+ *     receiver(s) in that order;
+ *   - the same result by a second valid processing order (Kahn topological
+ *     order), which Sec. 3.2 says must give identical water amounts;
+ *   - the matrix-free product y = A x (Sec. 3.1, "matrix-vector product with
+ *     A"; App. A for the multi-receiver form), used for residual checks;
+ *   - the adjoint g = A^{-T} gbar by a low-to-high sweep (A is lower triangular
+ *     in high-to-low numbering, Sec. 2.4, so A^T is upper triangular and is
+ *     solved from the lowest cell up), with dL/dr = g and dL/dz through the
+ *     MFD weights;
+ *   - per-cell helpers for sampled checks on grids too large for the sort:
+ *     upstream basin size by breadth-first search over reversed edges, and the
+ *     sink reached from a cell.
+ *
+ * Readings of the paper that this file fixes (the paper is silent on them):
+ *   - grid is row-major, idx = y*nx + x; neighbour k has offset (dx_k, dy_k)
+ *     in the scan order E(+1,0) N(0,-1) W(-1,0) S(0,+1) NE(+1,-1) NW(-1,-1)
+ *     SW(-1,+1) SE(+1,+1); SINK = 0xFF;
+ *   - D8 "steepest" compares slope_k = fl32(fl32(z_c - z_k) * c_k) with
+ *     c_orth = fl32(1/dx), c_diag = fl32(1/(sqrt(2) dx)), over neighbours that
+ *     are strictly lower; strict '>' so the first in scan order wins ties;
+ *     "lowest" (flag) compares fl32(z_c - z_k) instead;
+ *   - edge cells are sinks by default (they still receive water); with
+ *     FR_EDGE_ROUTE they route to in-grid lower neighbours like other cells;
+ *   - MFD: f_k = s_k^p / sum_j s_j^p over strictly lower neighbours,
+ *     s_k = (z_c - z_k)/d_k, all in FP64;
+ *   - a cell with no strictly lower neighbour is a sink (flats are sinks).
+ *
+ * Precision: FP64 for water and gradients, uint64 for unit-rain D8 areas.
+ * The only fp32 arithmetic is the D8 slope predicate, so that the receiver
+ * choice is defined bit-for-bit.  Compile with -ffp-contract=off.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_SINK 0xFFu
+#define OR_EDGE_ROUTE 1u
+#define OR_D8_LOWEST 2u
+
+static const int OFFX[8] = {+1, 0, -1, 0, +1, -1, -1, +1};
+static const int OFFY[8] = {0, -1, 0, +1, -1, -1, +1, +1};
+
+static int is_edge(int64_t x, int64_t y, int64_t nx, int64_t ny) {
+    return x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+}
+
+/* Local flow routing, D8 (Sec. 2.1: the neighbour that is lower and to which
+ * the downhill gradient is steepest; footnote: none at the boundary). */
+void or_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx, uint32_t flags,
+                     uint8_t* dir) {
+    float c_orth = (float)(1.0 / dx);
+    float c_diag = (float)(1.0 / (sqrt(2.0) * dx));
+    for (int64_t y = 0; y < ny; ++y) {
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t i = y * nx + x;
+            dir[i] = OR_SINK;
+            if (!(flags & OR_EDGE_ROUTE) && is_edge(x, y, nx, ny)) continue;
+            float zc = z[i];
+            float best = -1.0f;
+            for (int k = 0; k < 8; ++k) {
+                int64_t xn = x + OFFX[k], yn = y + OFFY[k];
+                if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+                float zn = z[yn * nx + xn];
+                if (!(zn < zc)) continue;
+                float drop = zc - zn;
+                float s;
+                if (flags & OR_D8_LOWEST) s = drop;
+                else s = drop * (k < 4 ? c_orth : c_diag);
+                if (s > best) { best = s; dir[i] = (uint8_t)k; }
+            }
+        }
+    }
+}
+
+/* Local flow routing, MFD (App. A): fractions of a cell's water given to each
+ * strictly lower neighbour, f_k = s_k^p / sum_j s_j^p, FP64.  frac is N x 8,
+ * zero where neighbour k is not a receiver.  mask bit k set iff f_k is a
+ * receiver. */
+void or_receivers_mfd(const double* z, int64_t nx, int64_t ny, double dx, double p, uint32_t flags,
+                      uint8_t* mask, double* frac) {
+    for (int64_t y = 0; y < ny; ++y) {
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t i = y * nx + x;
+            double u[8];
+            double tot = 0.0;
+            mask[i] = 0;
+            for (int k = 0; k < 8; ++k) { u[k] = 0.0; frac[i * 8 + k] = 0.0; }
+            if (!(flags & OR_EDGE_ROUTE) && is_edge(x, y, nx, ny)) continue;
+            double zc = z[i];
+            for (int k = 0; k < 8; ++k) {
+                int64_t xn = x + OFFX[k], yn = y + OFFY[k];
+                if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+                double zn = z[yn * nx + xn];
+                if (!(zn < zc)) continue;
+                double d = (k < 4) ? dx : sqrt(2.0) * dx;
+                double s = (zc - zn) / d;
+                u[k] = pow(s, p);
+                mask[i] |= (uint8_t)(1u << k);
+            }
+            for (int k = 0; k < 8; ++k) tot += u[k];
+            if (tot > 0.0)
+                for (int k = 0; k < 8; ++k) frac[i * 8 + k] = u[k] / tot;
+        }
+    }
+}
+
+/* Number of donors of each cell (cells whose routing sends water to it). */
+void or_indegree(const uint8_t* dir_or_mask, int is_mask, int64_t nx, int64_t ny, uint8_t* indeg) {
+    int64_t n = nx * ny;
+    memset(indeg, 0, (size_t)n);
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t i = y * nx + x;
+            for (int k = 0; k < 8; ++k) {
+                int sends = is_mask ? ((dir_or_mask[i] >> k) & 1) : (dir_or_mask[i] == k);
+                if (!sends) continue;
+                indeg[(y + OFFY[k]) * nx + (x + OFFX[k])] += 1;
+            }
+        }
+}
+
+/* ---- high-to-low order (Sec. 2.1: sort all nodes from high to low) ---- */
+static const float* g_sort_z;
+static int cmp_high_to_low(const void* a, const void* b) {
+    int64_t ia = *(const int64_t*)a, ib = *(const int64_t*)b;
+    float za = g_sort_z[ia], zb = g_sort_z[ib];
+    if (za > zb) return -1;
+    if (za < zb) return 1;
+    return (ia < ib) ? -1 : (ia > ib);
+}
+
+static const double* g_sort_z64;
+static int cmp_high_to_low64(const void* a, const void* b) {
+    int64_t ia = *(const int64_t*)a, ib = *(const int64_t*)b;
+    double za = g_sort_z64[ia], zb = g_sort_z64[ib];
+    if (za > zb) return -1;
+    if (za < zb) return 1;
+    return (ia < ib) ? -1 : (ia > ib);
+}
+
+/* Same order for FP64 elevations (used when elevations are perturbed in FP64
+ * for finite-difference checks of the elevation gradient). */
+void or_high_to_low_order64(const double* z, int64_t n, int64_t* order) {
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    g_sort_z64 = z;
+    qsort(order, (size_t)n, sizeof(int64_t), cmp_high_to_low64);
+}
+
+/* order[0..n) = cell indices sorted by (z descending, index ascending).
+ * Any order in which every cell comes after all of its higher neighbours is
+ * valid (Sec. 3.2); water only moves to strictly lower cells, so this is one. */
+void or_high_to_low_order(const float* z, int64_t n, int64_t* order) {
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    g_sort_z = z;
+    qsort(order, (size_t)n, sizeof(int64_t), cmp_high_to_low);
+}
+
+/* Global flow routing, D8 (Eq. high-to-low-procedure; listing "global flow
+ * routing"): w = r, then for src high-to-low: w(dst) += w(src).
+ * rain == NULL means unit rain.  w (FP64) and/or area (uint64, unit rain)
+ * may be NULL. */
+void or_accumulate_d8(const uint8_t* dir, const int64_t* order, const float* rain,
+                      int64_t nx, int64_t ny, double* w, uint64_t* area) {
+    int64_t n = nx * ny;
+    if (w) for (int64_t i = 0; i < n; ++i) w[i] = rain ? (double)rain[i] : 1.0;
+    if (area) for (int64_t i = 0; i < n; ++i) area[i] = 1;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t src = order[t];
+        uint8_t d = dir[src];
+        if (d == OR_SINK) continue;
+        int64_t dst = src + OFFY[d] * nx + OFFX[d];
+        if (w) w[dst] += w[src];
+        if (area) area[dst] += area[src];
+    }
+}
+
+/* Global flow routing, MFD (App. A: each column of A holds the fractions):
+ * w = r, then for src high-to-low: w(dst_k) += f_k w(src). */
+void or_accumulate_mfd(const double* frac, const int64_t* order, const float* rain,
+                       int64_t nx, int64_t ny, double* w) {
+    int64_t n = nx * ny;
+    for (int64_t i = 0; i < n; ++i) w[i] = rain ? (double)rain[i] : 1.0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t src = order[t];
+        for (int k = 0; k < 8; ++k) {
+            double f = frac[src * 8 + k];
+            if (f == 0.0) continue;
+            w[src + OFFY[k] * nx + OFFX[k]] += f * w[src];
+        }
+    }
+}
+
+/* A second valid processing order: Kahn's algorithm (a cell is ready once all
+ * of its donors are done).  Sec. 3.2: only the processing order matters, so
+ * the water amounts must equal those of the high-to-low sort.
+ * dir_or_mask as in or_indegree; order_out receives the Kahn order. */
+int64_t or_kahn_order(const uint8_t* dir_or_mask, int is_mask, int64_t nx, int64_t ny,
+                      int64_t* order_out) {
+    int64_t n = nx * ny;
+    uint8_t* cnt = (uint8_t*)malloc((size_t)n);
+    or_indegree(dir_or_mask, is_mask, nx, ny, cnt);
+    int64_t head = 0, tail = 0;
+    for (int64_t i = 0; i < n; ++i) if (cnt[i] == 0) order_out[tail++] = i;
+    while (head < tail) {
+        int64_t c = order_out[head++];
+        int64_t x = c % nx, y = c / nx;
+        for (int k = 0; k < 8; ++k) {
+            int sends = is_mask ? ((dir_or_mask[c] >> k) & 1) : (dir_or_mask[c] == k);
+            if (!sends) continue;
+            int64_t d = (y + OFFY[k]) * nx + (x + OFFX[k]);
+            if (--cnt[d] == 0) order_out[tail++] = d;
+        }
+    }
+    free(cnt);
+    return tail; /* == n unless the routing has a cycle */
+}
+
+/* Matrix-free y = A x (Sec. 3.1 "matrix-vector product with A; optimized", and
+ * the multi-receiver form of App. A): y = x, then y(dst) -= f * x(src). */
+void or_apply_A(const uint8_t* dir, const double* frac, int64_t nx, int64_t ny,
+                const double* x, double* y) {
+    int64_t n = nx * ny;
+    for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+    for (int64_t src = 0; src < n; ++src) {
+        if (frac) {
+            for (int k = 0; k < 8; ++k) {
+                double f = frac[src * 8 + k];
+                if (f != 0.0) y[src + OFFY[k] * nx + OFFX[k]] -= f * x[src];
+            }
+        } else {
+            uint8_t d = dir[src];
+            if (d != OR_SINK) y[src + OFFY[d] * nx + OFFX[d]] -= x[src];
+        }
+    }
+}
+
+/* Adjoint: g = A^{-T} gbar.  Column src of A holds +1 on the diagonal and -f_k
+ * in rows dst_k, so row src of A^T reads g(src) - sum_k f_k g(dst_k) = gbar(src).
+ * Receivers are strictly lower, so a low-to-high sweep (the high-to-low order
+ * reversed) has every g(dst_k) ready when src is reached.
+ * frac == NULL selects D8 (dir).  gbar == NULL selects the loss
+ * L = sum over sinks of w_s^2, i.e. gbar_s = 2 w_s at sinks and 0 elsewhere.
+ * Returns g in g_out (== dL/dr). */
+void or_adjoint(const uint8_t* dir, const double* frac, const int64_t* order,
+                int64_t nx, int64_t ny, const double* w, const double* gbar, double* g) {
+    int64_t n = nx * ny;
+    for (int64_t i = 0; i < n; ++i) {
+        if (gbar) { g[i] = gbar[i]; continue; }
+        int sink;
+        if (frac) {
+            sink = 1;
+            for (int k = 0; k < 8; ++k) if (frac[i * 8 + k] != 0.0) sink = 0;
+        } else {
+            sink = (dir[i] == OR_SINK);
+        }
+        g[i] = sink ? 2.0 * w[i] : 0.0;
+    }
+    for (int64_t t = n - 1; t >= 0; --t) {
+        int64_t src = order[t];
+        int64_t x = src % nx, y = src / nx;
+        if (frac) {
+            double acc = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                double f = frac[src * 8 + k];
+                if (f != 0.0) acc += f * g[(y + OFFY[k]) * nx + (x + OFFX[k])];
+            }
+            g[src] += acc;
+        } else {
+            uint8_t d = dir[src];
+            if (d != OR_SINK) g[src] += g[(y + OFFY[d]) * nx + (x + OFFX[d])];
+        }
+    }
+}
+
+/* dL/dz for the MFD rule, given w = A^{-1} r and g = A^{-T} gbar.
+ * dL/dtheta = g^T (dW/dtheta) w with W(dst_k, src) = f_k(src).  The fractions
+ * of src depend on z_src and on z of its lower neighbours:
+ *   u_k = s_k^p, s_k = (z_src - z_k)/d_k, f_k = u_k / S, S = sum_j u_j,
+ *   dL/du_j = w_src (g_{dst_j} - G) / S,  G = sum_k f_k g_{dst_k},
+ *   du_j/dz_src = p s_j^{p-1} / d_j = -du_j/dz_{dst_j}.
+ * The lower set is held fixed (the derivative where it is constant). */
+void or_mfd_grad_z(const double* z, int64_t nx, int64_t ny, double dx, double p, uint32_t flags,
+                   const double* frac, const double* w, const double* g, double* dLdz) {
+    int64_t n = nx * ny;
+    for (int64_t i = 0; i < n; ++i) dLdz[i] = 0.0;
+    for (int64_t y = 0; y < ny; ++y) {
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t src = y * nx + x;
+            double s[8], u[8], S = 0.0, G = 0.0;
+            int any = 0;
+            for (int k = 0; k < 8; ++k) {
+                s[k] = 0.0; u[k] = 0.0;
+                if (frac[src * 8 + k] == 0.0) continue;
+                int64_t dst = (y + OFFY[k]) * nx + (x + OFFX[k]);
+                double d = (k < 4) ? dx : sqrt(2.0) * dx;
+                s[k] = (z[src] - z[dst]) / d;
+                u[k] = pow(s[k], p);
+                S += u[k];
+                any = 1;
+            }
+            if (!any) continue;
+            for (int k = 0; k < 8; ++k) {
+                if (u[k] == 0.0) continue;
+                int64_t dst = (y + OFFY[k]) * nx + (x + OFFX[k]);
+                G += (u[k] / S) * g[dst];
+            }
+            for (int k = 0; k < 8; ++k) {
+                if (u[k] == 0.0) continue;
+                int64_t dst = (y + OFFY[k]) * nx + (x + OFFX[k]);
+                double d = (k < 4) ? dx : sqrt(2.0) * dx;
+                double dLdu = w[src] * (g[dst] - G) / S;
+                double dudz = p * pow(s[k], p - 1.0) / d;
+                dLdz[src] += dLdu * dudz;
+                dLdz[dst] -= dLdu * dudz;
+            }
+        }
+    }
+    (void)flags;
+}
+
+/* Mass balance (Sec. 4: outflow equals total rain): out[0] = sum of w over
+ * sinks, out[1] = sum of r.  frac == NULL selects D8. */
+void or_mass_balance(const uint8_t* dir, const uint8_t* mask, int64_t n, const float* rain,
+                     const double* w, double* out) {
+    double s = 0.0, r = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        int sink = mask ? (mask[i] == 0) : (dir[i] == OR_SINK);
+        if (sink) s += w[i];
+        r += rain ? (double)rain[i] : 1.0;
+    }
+    out[0] = s;
+    out[1] = r;
+}
+
+/* Upstream basin size of one cell by breadth-first search over reversed D8
+ * edges (the cell itself included): equals the unit-rain area at that cell.
+ * work must hold nx*ny int64 entries; seen must hold nx*ny bytes, all zero on
+ * entry; both are restored/zeroed on exit so the call can be repeated. */
+uint64_t or_upstream_count(const uint8_t* dir, int64_t nx, int64_t ny, int64_t cell,
+                           int64_t* work, uint8_t* seen) {
+    int64_t head = 0, tail = 0;
+    work[tail++] = cell;
+    seen[cell] = 1;
+    while (head < tail) {
+        int64_t c = work[head++];
+        int64_t x = c % nx, y = c / nx;
+        for (int k = 0; k < 8; ++k) {
+            int64_t xn = x + OFFX[k], yn = y + OFFY[k];
+            if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+            int64_t nb = yn * nx + xn;
+            /* nb donates to c iff its direction points back at c */
+            int back = (k < 4) ? ((k + 2) & 3) : (4 + ((k - 4 + 2) & 3));
+            if (dir[nb] == back && !seen[nb]) { seen[nb] = 1; work[tail++] = nb; }
+        }
+    }
+    for (int64_t t = 0; t < tail; ++t) seen[work[t]] = 0;
+    return (uint64_t)tail;
+}
+
+/* Sink reached from a cell by following D8 receivers (-1 if the walk exceeds
+ * nx*ny steps, i.e. a cycle). */
+int64_t or_sink_of(const uint8_t* dir, int64_t nx, int64_t ny, int64_t cell) {
+    int64_t c = cell;
+    for (int64_t steps = 0; steps <= nx * ny; ++steps) {
+        uint8_t d = dir[c];
+        if (d == OR_SINK) return c;
+        c += OFFY[d] * nx + OFFX[d];
+    }
+    return -1;
+}
