@@ -1,0 +1,255 @@
+/*
+ * fr.h -- C ABI of the GB300 flow-routing library (libfr.so).
+ *
+ * The library computes the data-parallel hot path of W. Bangerth, "Massively
+ * parallel flow routing and drainage area determination":
+ *   1. local flow routing: each DEM cell picks its receiver (D8 steepest
+ *      descent, Sec. 2.1) or splits its water among all lower neighbours with
+ *      slope-weighted fractions (MFD, App. A);
+ *   2. global flow routing: the amount of water w at every cell, the solution
+ *      of A w = r with A = I - W (Sec. 2.2, Eq. Aw=f), i.e. rain plus all water
+ *      received from upstream, computed exactly (the result of the sequential
+ *      high-to-low algorithm of Sec. 2.1);
+ *   3. the adjoint of step 2 (gradients of a loss with respect to rain and,
+ *      for MFD, elevation), a batched form over many independent DEMs, and a
+ *      mass-balance check (Sec. 4: outflow equals total rain).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      row-major, cell (x, y) at index y*nx + x, 0 <= x < nx (fastest).
+ * Neighbour codes k = 0..7 in the scan order E(+1,0) N(0,-1) W(-1,0) S(0,+1)
+ *           NE(+1,-1) NW(-1,-1) SW(-1,+1) SE(+1,+1); FR_SINK (0xFF) = no
+ *           receiver.  Orthogonal distance dx, diagonal sqrt(2)*dx.
+ * Memory    every array argument is a DEVICE pointer to caller-owned memory
+ *           (cudaMalloc or equivalent), unless stated otherwise.  The library
+ *           allocates nothing in these calls; scratch comes from the caller's
+ *           workspace `ws` of at least the size returned by the matching
+ *           *_workspace_size query, 256-byte aligned.  Workspace contents need
+ *           not be initialised and are not preserved between calls.
+ * Streams   `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *           stream).  All work is enqueued on it; calls return without
+ *           synchronising.  Inputs must stay valid and outputs must not be
+ *           read until the stream has reached the end of the call.
+ * Errors    argument errors are detected synchronously and returned before
+ *           anything is enqueued.  Launch errors return FR_ERR_CUDA.  Errors
+ *           found on the device (a routing graph with a cycle, a device-side
+ *           wait that reached its limit) are written to a status word inside
+ *           the workspace; read it with fr_get_status() after the stream has
+ *           synchronised.  On a device-side error the outputs are unspecified.
+ * Flags     bit-or of the FR_* flag macros below; unknown bits are rejected.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FR_OK = 0,
+    FR_ERR_INVALID_ARG = 1, /* null pointer, non-positive size, bad flag, nx*ny overflow */
+    FR_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+    FR_ERR_WORKSPACE = 3,   /* workspace NULL, too small or not 256-byte aligned */
+    FR_ERR_NONFINITE = 4,   /* FR_CHECK_FINITE: the DEM holds NaN or Inf */
+    FR_ERR_NO_PROGRESS = 5, /* device: not every cell was reached (cycle in the routing) */
+    FR_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} fr_status;
+
+/* ---- flags ---------------------------------------------------------------
+ * Edge cells (x == 0, y == 0, x == nx-1, y == ny-1).  The paper's footnote to
+ * Sec. 2.1 gives boundary cells no receiver; its Fig. 1 example routes them.
+ *   FR_EDGE_SINK  (default) edge cells are sinks; they still receive water.
+ *   FR_EDGE_ROUTE edge cells route to in-grid lower neighbours like any cell.
+ * D8 rule.  Sec. 2.1 picks the lower neighbour with the steepest downhill
+ * gradient; the introduction speaks of the lowest-lying neighbour.
+ *   FR_D8_STEEPEST (default) maximise fl32(fl32(z_c - z_k) * c_k),
+ *                  c_orth = fl32(1/dx), c_diag = fl32(1/(sqrt(2)*dx)).
+ *   FR_D8_LOWEST   maximise fl32(z_c - z_k).
+ * Both consider only strictly lower neighbours (flats are sinks) and break
+ * ties with strict '>' in scan order (the first code wins).
+ *   FR_CHECK_FINITE reject a DEM holding NaN or Inf (FR_ERR_NONFINITE; this
+ *                  check synchronises the stream).
+ */
+#define FR_EDGE_SINK 0x0u
+#define FR_EDGE_ROUTE 0x1u
+#define FR_D8_STEEPEST 0x0u
+#define FR_D8_LOWEST 0x2u
+#define FR_CHECK_FINITE 0x4u
+
+#define FR_SINK 0xFFu
+
+typedef enum { FR_ROUTING_D8 = 0, FR_ROUTING_MFD = 1 } fr_routing_kind;
+
+/* Operation codes for fr_workspace_size. */
+typedef enum {
+    FR_OP_RECEIVERS = 0,
+    FR_OP_ACCUMULATE = 1,
+    FR_OP_ADJOINT = 2,
+    FR_OP_MASS_BALANCE = 3,
+    FR_OP_ROUTE = 4 /* receivers + accumulate in one call (fr_route_d8/_mfd) */
+} fr_op;
+
+/*
+ * Local flow routing, D8 (Sec. 2.1, footnote 2; App. A first paragraph).
+ *   dem       [ny*nx] float32 elevations (metres).
+ *   nx, ny    grid size, both >= 1, nx*ny < 2^40.
+ *   dx        grid spacing (> 0, finite); only the slope rule depends on it.
+ *   flags     FR_EDGE_*, FR_D8_*, FR_CHECK_FINITE.
+ *   dir_out   [ny*nx] uint8: receiver code 0..7 or FR_SINK.
+ *   indeg_out [ny*nx] uint8 or NULL: number of donors of each cell (0..8).
+ * Results are bit-identical to the rule stated above.
+ */
+fr_status fr_receivers_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
+                          uint8_t* dir_out, uint8_t* indeg_out, void* stream);
+
+/*
+ * Local flow routing, multiple flow directions (App. A: water split among
+ * the lower neighbours with fractions f_k; Freeman-style slope weights).
+ *   f_k = s_k^p / sum_j s_j^p over strictly lower neighbours j,
+ *   s_k = (z_c - z_k) / d_k, d_k = dx or sqrt(2)*dx.
+ *   mask_out  [ny*nx] uint8: bit k set iff neighbour k receives water
+ *             (0 = sink).
+ *   frac_out  [ny*nx*8] float32 or NULL: f_k per cell and code, 0 where bit k
+ *             is clear.  Computed in fp32 with a compensated normaliser.
+ *   indeg_out [ny*nx] uint8 or NULL: number of donors.
+ *   p         exponent, finite, > 0 (1.1 in the benchmark configuration).
+ */
+fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
+                           uint32_t flags, uint8_t* mask_out, float* frac_out,
+                           uint8_t* indeg_out, void* stream);
+
+/* Routing description consumed by fr_accumulate / fr_route_adjoint /
+ * fr_mass_balance.  All pointers are device pointers. */
+typedef struct {
+    int32_t kind;         /* FR_ROUTING_D8 or FR_ROUTING_MFD */
+    int32_t reserved;     /* must be 0 */
+    int64_t nx, ny;
+    const uint8_t* dir;   /* D8: [ny*nx] codes from fr_receivers_d8 */
+    const uint8_t* mask;  /* MFD: [ny*nx] receiver masks from fr_receivers_mfd */
+    const float* dem;     /* MFD: [ny*nx] elevations; fractions are recomputed
+                             from them (same arithmetic as fr_receivers_mfd) */
+    double dx;            /* MFD: grid spacing */
+    double p;             /* MFD: slope exponent */
+    uint32_t flags;       /* MFD: the flags given to fr_receivers_mfd */
+    uint32_t reserved2;   /* must be 0 */
+} fr_routing;
+
+/*
+ * Global flow routing: w = A^{-1} r (Sec. 2.2), the exact result of the
+ * high-to-low algorithm (Sec. 2.1, Eq. high-to-low-procedure) computed in
+ * parallel.  Every cell holds its own rain plus everything its donors pass
+ * on; sinks keep their water.
+ *   rain      [ny*nx] float32 >= 0, or NULL for unit rain (1 per cell).
+ *   w_out     [ny*nx] float32 or NULL: water per cell, the leading word of a
+ *             compensated two-float sum (error a few units in the last place
+ *             of fp32 for D8; see the design notes for MFD).
+ *   w_lo_out  [ny*nx] float32 or NULL: trailing word of that sum
+ *             (w ~= w_out + w_lo_out).
+ *   area_out  [ny*nx] uint64 or NULL: D8 only -- unit-rain drainage area in
+ *             cells (Sec. 1, "a note on terminology"), exact.  Ignores rain.
+ * At least one output must be non-NULL.  Requires ws of
+ * fr_workspace_size(FR_OP_ACCUMULATE, nx, ny, flags) bytes.
+ * A routing graph with a cycle leaves FR_ERR_NO_PROGRESS in the status word.
+ */
+fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_out,
+                        float* w_lo_out, uint64_t* area_out, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/*
+ * Receivers + accumulation in one call (D8): the direction grid goes to
+ * dir_out if non-NULL, else to the workspace.  Outputs as fr_accumulate.
+ * Workspace: fr_workspace_size(FR_OP_ROUTE, nx, ny, flags).
+ */
+fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
+                      const float* rain, float* w_out, float* w_lo_out, uint64_t* area_out,
+                      uint8_t* dir_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Receivers + accumulation in one call (MFD).  mask_out may be NULL. */
+fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
+                       uint32_t flags, const float* rain, float* w_out, float* w_lo_out,
+                       uint8_t* mask_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Adjoint of global flow routing.  With g = A^{-T} gbar (the transposed
+ * system: each cell's adjoint equals its own gbar plus the fraction-weighted
+ * adjoints of its receivers, so it is solved from the sinks upstream):
+ *   dLdr = g                              (dL/d rain)
+ *   dLdz = g^T (dW/dz) w                  (MFD only; through the fractions,
+ *                                          lower sets held fixed)
+ *   w, w_lo   forward result (w_lo may be NULL); used for gbar at sinks and
+ *             for dLdz.
+ *   dLdw      [ny*nx] float32 = gbar, or NULL for L = sum over sinks of w^2
+ *             (gbar = 2 w at sinks, 0 elsewhere).
+ *   dLdr_out  [ny*nx] float32 (required).
+ *   dLdz_out  [ny*nx] float32 or NULL; must be NULL for D8 (the D8 routing is
+ *             piecewise constant in z, so dL/dz = 0 almost everywhere).
+ * Workspace: fr_workspace_size(FR_OP_ADJOINT, nx, ny, flags).
+ */
+fr_status fr_route_adjoint(const fr_routing* routing, const float* w, const float* w_lo,
+                           const float* dLdw, float* dLdr_out, float* dLdz_out, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/*
+ * Mass balance (Sec. 4: the water leaving through the sinks equals the total
+ * rain).  Writes three doubles to out_dev (device memory):
+ *   out_dev[0] = sum over sinks of (w + w_lo)   (0 if w is NULL)
+ *   out_dev[1] = sum of rain (nx*ny for unit rain)
+ *   out_dev[2] = sum over sinks of area         (0 if area is NULL), exact
+ * The reduction order is fixed, so repeated calls give identical bits.
+ * Workspace: fr_workspace_size(FR_OP_MASS_BALANCE, nx, ny, flags).
+ */
+fr_status fr_mass_balance(const fr_routing* routing, const float* rain, const float* w,
+                          const float* w_lo, const uint64_t* area, double* out_dev, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/* One independent DEM of a batch (all pointers device pointers). */
+typedef struct {
+    const float* dem;   /* [ny*nx] */
+    const float* rain;  /* [ny*nx] or NULL (unit rain) */
+    float* w_out;       /* [ny*nx] or NULL */
+    float* w_lo_out;    /* [ny*nx] or NULL */
+    uint64_t* area_out; /* [ny*nx] or NULL; D8 only */
+    uint8_t* route_out; /* [ny*nx] direction codes (D8) / masks (MFD), required */
+    int64_t nx, ny;
+    double dx;
+} fr_tile;
+
+/*
+ * Batched routing of many independent DEMs of uneven size (receivers +
+ * accumulation for every tile) with one launch per stage over all tiles,
+ * CTAs taking work from a device-side queue; the sequence can be captured in
+ * a CUDA graph.
+ *   tiles_host  [ntiles] host array (read during the call only).
+ *   tiles_dev   [ntiles] device copy of the same array, provided by the
+ *               caller (so that no host memory is read at execution time).
+ *   kind        FR_ROUTING_D8 or FR_ROUTING_MFD; p the MFD exponent.
+ * Workspace: fr_batch_workspace_size(tiles_host, ntiles, kind, flags).
+ */
+fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
+                         int32_t kind, double p, uint32_t flags, void* ws, size_t ws_bytes,
+                         void* stream);
+size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_t kind,
+                               uint32_t flags);
+
+/* Workspace bytes an operation needs for an nx-by-ny grid (0 if the sizes
+ * are invalid).  FR_OP_RECEIVERS needs none. */
+size_t fr_workspace_size(int32_t op, int64_t nx, int64_t ny, uint32_t flags);
+
+/* Synchronises `stream`, then reads and clears the device status word kept
+ * in the workspace of the last call that used `ws`. */
+fr_status fr_get_status(const void* ws, size_t ws_bytes, void* stream);
+
+/* Static English description of a status code. */
+const char* fr_status_string(fr_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t fr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FR_H */

@@ -1,0 +1,232 @@
+"""Python API over the C ABI (torch tensors in, torch tensors out).
+
+PyTorch supplies device memory and the current CUDA stream; all arithmetic
+runs in libfr.so.  Functions accept CUDA tensors; the ``route_*`` helpers also
+accept CPU tensors (pinned memory recommended), in which case the inputs are
+copied to the GPU and the results copied back (the end-to-end path).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, Optional
+
+import torch
+
+from . import _lib
+from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_ROUTE, check, fr_routing, load)
+
+_ws_cache: Dict[int, torch.Tensor] = {}
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_grid(t: torch.Tensor, dtype, name: str):
+    if t.dim() != 2:
+        raise ValueError("%s must be 2-D (ny, nx)" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+def workspace(nx: int, ny: int, device=None) -> torch.Tensor:
+    """A cached workspace large enough for any operation on an nx-by-ny grid."""
+    dev = torch.device(device if device is not None else "cuda")
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    need = int(load().fr_workspace_size(FR_OP_ROUTE, nx, ny, 0))
+    if need == 0:
+        raise ValueError("invalid grid size %dx%d" % (nx, ny))
+    ws = _ws_cache.get(idx)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=torch.device("cuda", idx))
+        _ws_cache[idx] = ws
+    return ws
+
+
+def routing_d8(dir_: torch.Tensor) -> fr_routing:
+    R = fr_routing()
+    R.kind = FR_ROUTING_D8
+    R.ny, R.nx = dir_.shape
+    R.dir = dir_.data_ptr()
+    return R
+
+
+def routing_mfd(mask: torch.Tensor, dem: torch.Tensor, dx: float, p: float, flags: int = 0) -> fr_routing:
+    R = fr_routing()
+    R.kind = FR_ROUTING_MFD
+    R.ny, R.nx = mask.shape
+    R.mask = mask.data_ptr()
+    R.dem = dem.data_ptr()
+    R.dx = dx
+    R.p = p
+    R.flags = flags
+    return R
+
+
+def receivers_d8(dem: torch.Tensor, dx: float = 30.0, flags: int = 0, indeg: bool = False):
+    """D8 receiver codes (uint8; 0..7 or 255), optionally donor counts."""
+    _check_grid(dem, torch.float32, "dem")
+    ny, nx = dem.shape
+    d = torch.empty((ny, nx), dtype=torch.uint8, device=dem.device)
+    n = torch.empty_like(d) if indeg else None
+    check(load().fr_receivers_d8(_p(dem), nx, ny, dx, flags, _p(d), _p(n), _stream()),
+          "fr_receivers_d8")
+    return (d, n) if indeg else d
+
+
+def receivers_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1, flags: int = 0,
+                  frac: bool = False, indeg: bool = False):
+    """MFD receiver masks (uint8), optionally fractions (ny, nx, 8) and donor counts."""
+    _check_grid(dem, torch.float32, "dem")
+    ny, nx = dem.shape
+    m = torch.empty((ny, nx), dtype=torch.uint8, device=dem.device)
+    f = torch.empty((ny, nx, 8), dtype=torch.float32, device=dem.device) if frac else None
+    n = torch.empty_like(m) if indeg else None
+    check(load().fr_receivers_mfd(_p(dem), nx, ny, dx, p, flags, _p(m), _p(f), _p(n), _stream()),
+          "fr_receivers_mfd")
+    out = (m,)
+    if frac:
+        out += (f,)
+    if indeg:
+        out += (n,)
+    return out if len(out) > 1 else m
+
+
+def accumulate(R: fr_routing, rain: Optional[torch.Tensor] = None, want_w: bool = True,
+               want_lo: bool = False, want_area: bool = False, device=None) -> Dict[str, torch.Tensor]:
+    """Water per cell for a routing (D8 or MFD); see fr_accumulate."""
+    ny, nx = R.ny, R.nx
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    if rain is not None:
+        _check_grid(rain, torch.float32, "rain")
+        dev = rain.device
+    out: Dict[str, torch.Tensor] = {}
+    w = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_w else None
+    lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
+    a = torch.empty((ny, nx), dtype=torch.int64, device=dev) if want_area else None
+    ws = workspace(nx, ny, dev)
+    check(load().fr_accumulate(ctypes.byref(R), _p(rain), _p(w), _p(lo), _p(a), _p(ws),
+                               ws.numel(), _stream()), "fr_accumulate")
+    if w is not None:
+        out["w"] = w
+    if lo is not None:
+        out["w_lo"] = lo
+    if a is not None:
+        out["area"] = a
+    return out
+
+
+def _to_cuda(t):
+    if t is None or t.is_cuda:
+        return t, False
+    return t.to("cuda", non_blocking=True), True
+
+
+def route_d8(dem: torch.Tensor, dx: float = 30.0, rain: Optional[torch.Tensor] = None,
+             flags: int = 0, want_w: bool = True, want_lo: bool = False, want_area: bool = True,
+             want_dir: bool = False) -> Dict[str, torch.Tensor]:
+    """Receivers + accumulation (D8) in one call (fr_route_d8).
+
+    CPU inputs are copied to the GPU and the outputs back to the CPU."""
+    dem_d, host = _to_cuda(dem)
+    rain_d, _ = _to_cuda(rain)
+    _check_grid(dem_d, torch.float32, "dem")
+    ny, nx = dem_d.shape
+    dev = dem_d.device
+    w = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_w else None
+    lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
+    a = torch.empty((ny, nx), dtype=torch.int64, device=dev) if want_area else None
+    d = torch.empty((ny, nx), dtype=torch.uint8, device=dev) if want_dir else None
+    ws = workspace(nx, ny, dev)
+    check(load().fr_route_d8(_p(dem_d), nx, ny, dx, flags, _p(rain_d), _p(w), _p(lo), _p(a), _p(d),
+                             _p(ws), ws.numel(), _stream()), "fr_route_d8")
+    out = {k: v for k, v in (("w", w), ("w_lo", lo), ("area", a), ("dir", d)) if v is not None}
+    if host:
+        out = {k: v.to("cpu") for k, v in out.items()}
+    return out
+
+
+def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
+              rain: Optional[torch.Tensor] = None, flags: int = 0, want_lo: bool = False,
+              want_mask: bool = False) -> Dict[str, torch.Tensor]:
+    """Receivers + accumulation (MFD) in one call (fr_route_mfd)."""
+    dem_d, host = _to_cuda(dem)
+    rain_d, _ = _to_cuda(rain)
+    _check_grid(dem_d, torch.float32, "dem")
+    ny, nx = dem_d.shape
+    dev = dem_d.device
+    w = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
+    m = torch.empty((ny, nx), dtype=torch.uint8, device=dev) if want_mask else None
+    ws = workspace(nx, ny, dev)
+    check(load().fr_route_mfd(_p(dem_d), nx, ny, dx, p, flags, _p(rain_d), _p(w), _p(lo), _p(m),
+                              _p(ws), ws.numel(), _stream()), "fr_route_mfd")
+    out = {k: v for k, v in (("w", w), ("w_lo", lo), ("mask", m)) if v is not None}
+    if host:
+        out = {k: v.to("cpu") for k, v in out.items()}
+    return out
+
+
+def adjoint(R: fr_routing, w: torch.Tensor, w_lo: Optional[torch.Tensor] = None,
+            dLdw: Optional[torch.Tensor] = None, want_dz: bool = False):
+    """(dL/dr, dL/dz or None) for L = sum over sinks of w^2, or for the
+    incoming gradient dLdw (fr_route_adjoint)."""
+    ny, nx = R.ny, R.nx
+    dev = w.device
+    dLdr = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    dLdz = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_dz else None
+    ws = workspace(nx, ny, dev)
+    check(load().fr_route_adjoint(ctypes.byref(R), _p(w), _p(w_lo), _p(dLdw), _p(dLdr), _p(dLdz),
+                                  _p(ws), ws.numel(), _stream()), "fr_route_adjoint")
+    return dLdr, dLdz
+
+
+def mass_balance(R: fr_routing, rain=None, w=None, w_lo=None, area=None, device=None) -> torch.Tensor:
+    """Device tensor [sum over sinks of w, sum of rain, sum over sinks of area]."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    ws = workspace(R.nx, R.ny, dev)
+    check(load().fr_mass_balance(ctypes.byref(R), _p(rain), _p(w), _p(w_lo), _p(area), _p(out),
+                                 _p(ws), ws.numel(), _stream()), "fr_mass_balance")
+    return out
+
+
+def get_status(device=None) -> int:
+    """Synchronises the current stream and returns (and clears) the device
+    status word of the cached workspace (0 = ok)."""
+    dev = torch.device(device if device is not None else "cuda")
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    ws = _ws_cache.get(idx)
+    if ws is None:
+        return 0
+    return int(load().fr_get_status(_p(ws), ws.numel(), _stream()))
+
+
+class RouteMFD(torch.autograd.Function):
+    """w = route_mfd(dem, rain) with a hand-written adjoint backward
+    (gradients with respect to the elevations and the rain)."""
+
+    @staticmethod
+    def forward(ctx, dem, rain, dx: float = 30.0, p: float = 1.1, flags: int = 0):
+        mask = receivers_mfd(dem, dx, p, flags)
+        R = routing_mfd(mask, dem, dx, p, flags)
+        out = accumulate(R, rain, want_w=True, want_lo=True, device=dem.device)
+        ctx.save_for_backward(dem, mask, out["w"], out["w_lo"])
+        ctx.cfg = (dx, p, flags)
+        return out["w"]
+
+    @staticmethod
+    def backward(ctx, grad_w):
+        dem, mask, w, w_lo = ctx.saved_tensors
+        dx, p, flags = ctx.cfg
+        R = routing_mfd(mask, dem, dx, p, flags)
+        dLdr, dLdz = adjoint(R, w, w_lo, dLdw=grad_w.contiguous().float(), want_dz=True)
+        return dLdz, dLdr, None, None, None

@@ -1,0 +1,283 @@
+// fr_accumulate.cu -- launches of the tile engine, the mass-balance reduction
+// and the MFD elevation-gradient stencil.
+#include "fr_engine.cuh"
+
+namespace fr {
+namespace {
+
+template <Mode M, bool W, bool A>
+cudaError_t launch_single(const Prob& P, EngineGlobals* G, cudaStream_t s) {
+    constexpr size_t sm = engine_smem<M, W, A>();
+    cudaError_t e = cudaFuncSetAttribute(k_engine<M, W, A>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles_y = (P.ny + kTileY - 1) / kTileY;
+    const int64_t tiles = tiles_y * P.tiles_x;
+    k_engine<M, W, A><<<(unsigned)tiles, 256, sm, s>>>(P, G);
+    return cudaGetLastError();
+}
+
+template <Mode M, bool W, bool A>
+cudaError_t launch_batch(const Prob* probs, const int64_t* prefix, int nprob, int64_t total_tiles,
+                         unsigned long long total_cells, EngineGlobals* G, int grid,
+                         cudaStream_t s) {
+    constexpr size_t sm = engine_smem<M, W, A>();
+    cudaError_t e = cudaFuncSetAttribute(k_engine_batch<M, W, A>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_engine_batch<M, W, A><<<grid, 256, sm, s>>>(probs, prefix, nprob, total_tiles, total_cells, G);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- mass balance
+constexpr int MB_NT = 256;
+
+template <bool MFD>
+__global__ void __launch_bounds__(MB_NT) k_mass_partial(int64_t n, const uint8_t* __restrict__ rb,
+                                                        const float* __restrict__ rain,
+                                                        const float* __restrict__ w,
+                                                        const float* __restrict__ w_lo,
+                                                        const uint64_t* __restrict__ area,
+                                                        double* __restrict__ partials) {
+    df sw = df_make(0.0f), sr = df_make(0.0f);
+    unsigned long long sa = 0;
+    const int64_t stride = (int64_t)gridDim.x * MB_NT;
+    for (int64_t i = (int64_t)blockIdx.x * MB_NT + threadIdx.x; i < n; i += stride) {
+        uint8_t b = rb[i];
+        bool sink = MFD ? (b == 0) : (b == kSink);
+        sr = df_add(sr, df_make(rain ? rain[i] : 1.0f));
+        if (sink) {
+            if (w) sw = df_add(sw, df{w[i], w_lo ? w_lo[i] : 0.0f});
+            if (area) sa += area[i];
+        }
+    }
+    double v0 = (double)sw.hi + (double)sw.lo, v1 = (double)sr.hi + (double)sr.lo;
+    for (int o = 16; o; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+    }
+    __shared__ double s0[MB_NT / 32], s1[MB_NT / 32];
+    __shared__ unsigned long long s2[MB_NT / 32];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s0[warp] = v0;
+        s1[warp] = v1;
+        s2[warp] = sa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        unsigned long long c = 0;
+        for (int i = 0; i < MB_NT / 32; ++i) {
+            a += s0[i];
+            b += s1[i];
+            c += s2[i];
+        }
+        partials[3 * blockIdx.x + 0] = a;
+        partials[3 * blockIdx.x + 1] = b;
+        reinterpret_cast<unsigned long long*>(partials)[3 * blockIdx.x + 2] = c;
+    }
+}
+
+__global__ void k_mass_final(const double* __restrict__ partials, int nblocks, double* out) {
+    __shared__ double s0[256], s1[256];
+    __shared__ unsigned long long s2[256];
+    double a = 0.0, b = 0.0;
+    unsigned long long c = 0;
+    for (int i = threadIdx.x; i < nblocks; i += 256) {
+        a += partials[3 * i];
+        b += partials[3 * i + 1];
+        c += reinterpret_cast<const unsigned long long*>(partials)[3 * i + 2];
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    s2[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            s0[threadIdx.x] += s0[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s0[0];
+        out[1] = s1[0];
+        out[2] = (double)s2[0];
+    }
+}
+
+// ------------------------------------------------------ MFD elevation gradient
+// dL/dz = g^T (dW/dz) w with the lower sets held fixed.  For a source cell c
+// with lower neighbours j: u_j = s_j^p, S = sum u_j, f_j = u_j/S,
+// G = sum f_j g_j, and a_j = w_c (g_j - G)/S * p u_j/(s_j d_j); then
+// dL/dz_c += sum_j a_j and dL/dz_{j} -= a_j.  Each thread gathers the terms
+// that land on its own cell from itself and its eight neighbours.
+constexpr int GTX = 32, GTY = 16, GNT = 256;
+constexpr int GHX = GTX + 4, GHY = GTY + 4;  // two-cell halo
+
+struct SrcTerms {
+    float a_over_s[8];  // w_c (g_j - G)/S * p/(s_j d_j) * u_j  per code j (0 if not lower)
+};
+
+__device__ __forceinline__ void src_terms(const float* zs, const float* ghs, const float* gls,
+                                          const uint8_t* ms, float w_hi, float w_lo, int hx, int hy,
+                                          const MfdConst& mc, float (&a)[8]) {
+    const uint32_t m = ms[hy * GHX + hx];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.0f;
+    if (!m) return;
+    const float zc = zs[hy * GHX + hx];
+    float u[8];
+    df S = df_make(0.0f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        u[k] = 0.0f;
+        if ((m >> k) & 1u) {
+            u[k] = mfd_u_call(zc, zs[(hy + offy(k)) * GHX + hx + offx(k)], k, mc);
+            S = df_add(S, df_make(u[k]));
+        }
+    }
+    const df inv = df_recip(S);
+    df G = df_make(0.0f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!((m >> k) & 1u)) continue;
+        int j = (hy + offy(k)) * GHX + hx + offx(k);
+        G = df_add(G, df_mul(mfd_frac(u[k], inv), df{ghs[j], gls[j]}));
+    }
+    const df wc = {w_hi, w_lo};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!((m >> k) & 1u)) continue;
+        int j = (hy + offy(k)) * GHX + hx + offx(k);
+        df dg = df_add(df{ghs[j], gls[j]}, df{-G.hi, -G.lo});
+        float zj = zs[j];
+        float s = __fmul_rn(__fsub_rn(zc, zj), k < 4 ? mc.co_hi : mc.cd_hi);  // s_j
+        float dud_z = __fmul_rn(mc.p, __fdiv_rn(u[k], s));                     // p s^{p-1}/d * ... /(1/d)
+        dud_z = __fmul_rn(dud_z, k < 4 ? mc.co_hi : mc.cd_hi);                  // p s^{p-1} / d
+        df t = df_mul(df_mul(wc, dg), inv);
+        a[k] = __fmul_rn(t.hi, dud_z);
+    }
+}
+
+__global__ void __launch_bounds__(GNT) k_mfd_grad_z(Prob P, const float* __restrict__ g_hi,
+                                                    const float* __restrict__ g_lo,
+                                                    float* __restrict__ dLdz) {
+    __shared__ float zs[GHX * GHY], ghs[GHX * GHY], gls[GHX * GHY];
+    __shared__ uint8_t ms[GHX * GHY];
+    __shared__ float as[(GTY + 2) * (GTX + 2)][8];
+    const int64_t tiles_x = (P.nx + GTX - 1) / GTX;
+    const int64_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    const int64_t x0 = tx * GTX, y0 = ty * GTY;
+    for (int i = threadIdx.x; i < GHX * GHY; i += GNT) {
+        int hy = i / GHX, hx = i - hy * GHX;
+        int64_t gx = x0 + hx - 2, gy = y0 + hy - 2;
+        bool in = gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny;
+        int64_t gi = gy * P.nx + gx;
+        zs[i] = in ? P.z[gi] : __int_as_float(0x7f800000);
+        ghs[i] = in ? g_hi[gi] : 0.0f;
+        gls[i] = (in && g_lo) ? g_lo[gi] : 0.0f;
+        ms[i] = in ? P.rb[gi] : 0;
+    }
+    __syncthreads();
+    // source terms of the tile and its one-cell ring
+    for (int i = threadIdx.x; i < (GTX + 2) * (GTY + 2); i += GNT) {
+        int ry = i / (GTX + 2), rx = i - ry * (GTX + 2);
+        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
+        float a[8];
+        if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
+            int64_t gi = gy * P.nx + gx;
+            src_terms(zs, ghs, gls, ms, P.wf[gi], P.wf_lo ? P.wf_lo[gi] : 0.0f, rx + 1, ry + 1, P.mc, a);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) as[i][k] = a[k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < GTX * GTY; i += GNT) {
+        int ly = i / GTX, lx = i - ly * GTX;
+        int64_t gx = x0 + lx, gy = y0 + ly;
+        if (gx >= P.nx || gy >= P.ny) continue;
+        const int r = (ly + 1) * (GTX + 2) + lx + 1;
+        df acc = df_make(0.0f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = df_add(acc, df_make(as[r][k]));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            // neighbour in direction k gives to this cell along code opp(k)
+            int rn = (ly + 1 + offy(k)) * (GTX + 2) + lx + 1 + offx(k);
+            acc = df_add(acc, df_make(-as[rn][opp(k)]));
+        }
+        dLdz[gy * P.nx + gx] = acc.hi;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_engine(Mode mode, bool want_w, bool want_area, const Prob& P,
+                          EngineGlobals* G, cudaStream_t s) {
+    switch (mode) {
+        case Mode::FwdD8:
+            if (want_w && want_area) return launch_single<Mode::FwdD8, true, true>(P, G, s);
+            if (want_w) return launch_single<Mode::FwdD8, true, false>(P, G, s);
+            return launch_single<Mode::FwdD8, false, true>(P, G, s);
+        case Mode::FwdMfd:
+            return launch_single<Mode::FwdMfd, true, false>(P, G, s);
+        case Mode::AdjD8:
+            return launch_single<Mode::AdjD8, true, false>(P, G, s);
+        case Mode::AdjMfd:
+            return launch_single<Mode::AdjMfd, true, false>(P, G, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Prob* probs,
+                                const int64_t* prefix, int32_t nprob, int64_t total_tiles,
+                                unsigned long long total_cells, EngineGlobals* G, int grid,
+                                cudaStream_t s) {
+    switch (mode) {
+        case Mode::FwdD8:
+            if (want_w && want_area)
+                return launch_batch<Mode::FwdD8, true, true>(probs, prefix, nprob, total_tiles,
+                                                             total_cells, G, grid, s);
+            if (want_w)
+                return launch_batch<Mode::FwdD8, true, false>(probs, prefix, nprob, total_tiles,
+                                                              total_cells, G, grid, s);
+            return launch_batch<Mode::FwdD8, false, true>(probs, prefix, nprob, total_tiles,
+                                                          total_cells, G, grid, s);
+        case Mode::FwdMfd:
+            return launch_batch<Mode::FwdMfd, true, false>(probs, prefix, nprob, total_tiles,
+                                                           total_cells, G, grid, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_mfd_grad_z(const Prob& P, const float* g_hi, const float* g_lo, float* dLdz,
+                              cudaStream_t s) {
+    const int64_t tiles = ((P.nx + GTX - 1) / GTX) * ((P.ny + GTY - 1) / GTY);
+    k_mfd_grad_z<<<(unsigned)tiles, GNT, 0, s>>>(P, g_hi, g_lo, dLdz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t* rb,
+                                const float* rain, const float* w, const float* w_lo,
+                                const uint64_t* area, double* partials, int nblocks, double* out,
+                                cudaStream_t s) {
+    const int64_t n = nx * ny;
+    if (kind == 1)
+        k_mass_partial<true><<<nblocks, MB_NT, 0, s>>>(n, rb, rain, w, w_lo, area, partials);
+    else
+        k_mass_partial<false><<<nblocks, MB_NT, 0, s>>>(n, rb, rain, w, w_lo, area, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_mass_final<<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fr

@@ -1,0 +1,308 @@
+// fr_api.cu -- the C ABI declared in include/fr.h: argument validation,
+// workspace layout, status word and the launch sequences.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/fr.h"
+#include "fr_internal.h"
+
+namespace fr {
+namespace {
+
+constexpr int64_t kMaxCells = (int64_t)1 << 40;
+constexpr int kMassBlocks = 1024;
+constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE;
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Workspace layout (same for every operation on an nx*ny grid):
+//   globals (64 B) | arrival counters (1 B/cell) | trailing words (4 B/cell)
+//   | walker links (8 B/cell) | routing bytes (1 B/cell) | mass partials
+// The first two regions are zeroed by each engine call (one memset).
+struct Layout {
+    size_t cnt, lo, link, rb, partials, total, zero_bytes;
+};
+
+Layout layout(int64_t n) {
+    Layout L;
+    size_t off = 256;
+    L.cnt = off;
+    off += align256((size_t)n + 4);
+    L.zero_bytes = off;
+    L.lo = off;
+    off += align256((size_t)n * 4);
+    L.link = off;
+    off += align256((size_t)n * 8);
+    L.rb = off;
+    off += align256((size_t)n);
+    L.partials = off;
+    off += align256((size_t)kMassBlocks * 3 * 8);
+    L.total = off;
+    return L;
+}
+
+bool sizes_ok(int64_t nx, int64_t ny) {
+    return nx >= 1 && ny >= 1 && nx < kMaxCells && ny < kMaxCells && nx <= kMaxCells / ny;
+}
+
+fr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FR_OK : FR_ERR_CUDA; }
+
+bool ws_ok(const void* ws, size_t ws_bytes, int64_t n) {
+    return ws && ((uintptr_t)ws & 255) == 0 && ws_bytes >= layout(n).total;
+}
+
+// FR_CHECK_FINITE uses a counter in the library's own device memory (module
+// scope, allocated when the library is loaded) and synchronises the stream.
+__device__ unsigned long long g_nonfinite;
+std::mutex g_finite_mutex;
+
+fr_status check_finite(const float* z, int64_t n, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_finite_mutex);
+    unsigned long long zero = 0, got = 0;
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_nonfinite) != cudaSuccess) return FR_ERR_CUDA;
+    if (cudaMemcpyAsync(ptr, &zero, sizeof(zero), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FR_ERR_CUDA;
+    if (launch_count_nonfinite(z, n, (unsigned long long*)ptr, s) != cudaSuccess) return FR_ERR_CUDA;
+    if (cudaMemcpyAsync(&got, ptr, sizeof(got), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FR_ERR_CUDA;
+    return got ? FR_ERR_NONFINITE : FR_OK;
+}
+
+bool routing_ok(const fr_routing* R) {
+    if (!R || R->reserved || R->reserved2) return false;
+    if (!sizes_ok(R->nx, R->ny)) return false;
+    if (R->kind == FR_ROUTING_D8) return R->dir != nullptr;
+    if (R->kind == FR_ROUTING_MFD)
+        return R->mask && R->dem && std::isfinite(R->dx) && R->dx > 0 && std::isfinite(R->p) &&
+               R->p > 0 && (R->flags & ~kKnownFlags) == 0;
+    return false;
+}
+
+Prob base_prob(const fr_routing* R, char* ws) {
+    Layout L = layout(R->nx * R->ny);
+    Prob P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = R->nx;
+    P.ny = R->ny;
+    P.rb = R->kind == FR_ROUTING_D8 ? R->dir : R->mask;
+    P.z = R->kind == FR_ROUTING_MFD ? R->dem : nullptr;
+    P.cnt = reinterpret_cast<uint32_t*>(ws + L.cnt);
+    P.link = reinterpret_cast<int64_t*>(ws + L.link);
+    P.out_lo = reinterpret_cast<float*>(ws + L.lo);
+    P.mc = make_mfd_const(R->kind == FR_ROUTING_MFD ? R->dx : 1.0, R->kind == FR_ROUTING_MFD ? R->p : 1.0);
+    P.tiles_x = (int32_t)((R->nx + kTileX - 1) / kTileX);
+    return P;
+}
+
+}  // namespace
+}  // namespace fr
+
+using namespace fr;
+
+extern "C" {
+
+const char* fr_status_string(fr_status s) {
+    switch (s) {
+        case FR_OK: return "ok";
+        case FR_ERR_INVALID_ARG: return "invalid argument";
+        case FR_ERR_CUDA: return "CUDA error";
+        case FR_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+        case FR_ERR_NONFINITE: return "DEM holds NaN or Inf";
+        case FR_ERR_NO_PROGRESS: return "not every cell was reached (cycle in the routing)";
+        case FR_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+int32_t fr_version(void) { return 100; }
+
+size_t fr_workspace_size(int32_t op, int64_t nx, int64_t ny, uint32_t flags) {
+    if (!sizes_ok(nx, ny) || (flags & ~kKnownFlags)) return 0;
+    if (op == FR_OP_RECEIVERS) return 0;
+    if (op < 0 || op > FR_OP_ROUTE) return 0;
+    return layout(nx * ny).total;
+}
+
+fr_status fr_get_status(const void* ws, size_t ws_bytes, void* stream) {
+    if (!ws || ws_bytes < 256 || ((uintptr_t)ws & 255)) return FR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    EngineGlobals g;
+    if (cudaMemcpyAsync(&g, ws, sizeof(g), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FR_ERR_CUDA;
+    unsigned zero = 0;
+    const size_t off = offsetof(EngineGlobals, status);
+    if (cudaMemcpyAsync((char*)ws + off, &zero, sizeof(zero), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return FR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FR_ERR_CUDA;
+    return (fr_status)g.status;
+}
+
+fr_status fr_receivers_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
+                          uint8_t* dir_out, uint8_t* indeg_out, void* stream) {
+    if (!dem || !dir_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
+        (flags & ~kKnownFlags))
+        return FR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & FR_CHECK_FINITE) {
+        fr_status st = check_finite(dem, nx * ny, s);
+        if (st != FR_OK) return st;
+    }
+    return cuda_status(launch_receivers_d8(dem, nx, ny, dx, flags, dir_out, indeg_out, s));
+}
+
+fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
+                           uint32_t flags, uint8_t* mask_out, float* frac_out, uint8_t* indeg_out,
+                           void* stream) {
+    if (!dem || !mask_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
+        !std::isfinite(p) || p <= 0 || (flags & ~kKnownFlags))
+        return FR_ERR_INVALID_ARG;
+    if (frac_out && ((uintptr_t)frac_out & 15)) return FR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & FR_CHECK_FINITE) {
+        fr_status st = check_finite(dem, nx * ny, s);
+        if (st != FR_OK) return st;
+    }
+    return cuda_status(launch_receivers_mfd(dem, nx, ny, dx, p, flags, mask_out, frac_out,
+                                            indeg_out, s));
+}
+
+fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, float* w_lo_out,
+                        uint64_t* area_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!routing_ok(R)) return FR_ERR_INVALID_ARG;
+    if (!w_out && !w_lo_out && !area_out) return FR_ERR_INVALID_ARG;
+    if (w_lo_out && !w_out) return FR_ERR_INVALID_ARG;
+    if (R->kind == FR_ROUTING_MFD && (area_out || !w_out)) return FR_ERR_INVALID_ARG;
+    const int64_t n = R->nx * R->ny;
+    if (!ws_ok(ws, ws_bytes, n)) return FR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prob P = base_prob(R, (char*)ws);
+    P.init = rain;
+    P.out_hi = w_out;
+    if (w_lo_out) {
+        P.out_lo = w_lo_out;
+        P.lo_full = 1;
+    }
+    P.area = area_out;
+    const Layout L = layout(n);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, s);
+    if (e != cudaSuccess) return FR_ERR_CUDA;
+    const Mode m = R->kind == FR_ROUTING_D8 ? Mode::FwdD8 : Mode::FwdMfd;
+    return cuda_status(launch_engine(m, w_out != nullptr, area_out != nullptr, P,
+                                     reinterpret_cast<EngineGlobals*>(ws), s));
+}
+
+fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
+                      const float* rain, float* w_out, float* w_lo_out, uint64_t* area_out,
+                      uint8_t* dir_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || (flags & ~kKnownFlags))
+        return FR_ERR_INVALID_ARG;
+    if (!ws_ok(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
+    uint8_t* dir = dir_out ? dir_out : reinterpret_cast<uint8_t*>((char*)ws + layout(nx * ny).rb);
+    fr_status st = fr_receivers_d8(dem, nx, ny, dx, flags, dir, nullptr, stream);
+    if (st != FR_OK) return st;
+    fr_routing R;
+    std::memset(&R, 0, sizeof(R));
+    R.kind = FR_ROUTING_D8;
+    R.nx = nx;
+    R.ny = ny;
+    R.dir = dir;
+    R.dx = dx;
+    R.flags = flags & ~FR_CHECK_FINITE;
+    return fr_accumulate(&R, rain, w_out, w_lo_out, area_out, ws, ws_bytes, stream);
+}
+
+fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
+                       uint32_t flags, const float* rain, float* w_out, float* w_lo_out,
+                       uint8_t* mask_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || !std::isfinite(p) ||
+        p <= 0 || (flags & ~kKnownFlags))
+        return FR_ERR_INVALID_ARG;
+    if (!ws_ok(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
+    uint8_t* mask = mask_out ? mask_out : reinterpret_cast<uint8_t*>((char*)ws + layout(nx * ny).rb);
+    fr_status st = fr_receivers_mfd(dem, nx, ny, dx, p, flags, mask, nullptr, nullptr, stream);
+    if (st != FR_OK) return st;
+    fr_routing R;
+    std::memset(&R, 0, sizeof(R));
+    R.kind = FR_ROUTING_MFD;
+    R.nx = nx;
+    R.ny = ny;
+    R.mask = mask;
+    R.dem = dem;
+    R.dx = dx;
+    R.p = p;
+    R.flags = flags & ~FR_CHECK_FINITE;
+    return fr_accumulate(&R, rain, w_out, w_lo_out, nullptr, ws, ws_bytes, stream);
+}
+
+fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_lo,
+                           const float* dLdw, float* dLdr_out, float* dLdz_out, void* ws,
+                           size_t ws_bytes, void* stream) {
+    if (!routing_ok(R) || !w || !dLdr_out) return FR_ERR_INVALID_ARG;
+    if (dLdz_out && R->kind != FR_ROUTING_MFD) return FR_ERR_INVALID_ARG;
+    const int64_t n = R->nx * R->ny;
+    if (!ws_ok(ws, ws_bytes, n)) return FR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prob P = base_prob(R, (char*)ws);
+    P.init = dLdw;
+    P.wf = w;
+    P.wf_lo = w_lo;
+    P.out_hi = dLdr_out;
+    P.lo_full = dLdz_out ? 1 : 0;  // the elevation gradient reads every trailing word
+    const Layout L = layout(n);
+    if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return FR_ERR_CUDA;
+    const Mode m = R->kind == FR_ROUTING_D8 ? Mode::AdjD8 : Mode::AdjMfd;
+    cudaError_t e = launch_engine(m, true, false, P, reinterpret_cast<EngineGlobals*>(ws), s);
+    if (e != cudaSuccess) return FR_ERR_CUDA;
+    if (dLdz_out) {
+        e = launch_mfd_grad_z(P, dLdr_out, P.out_lo, dLdz_out, s);
+        if (e != cudaSuccess) return FR_ERR_CUDA;
+    }
+    return FR_OK;
+}
+
+fr_status fr_mass_balance(const fr_routing* R, const float* rain, const float* w,
+                          const float* w_lo, const uint64_t* area, double* out_dev, void* ws,
+                          size_t ws_bytes, void* stream) {
+    if (!routing_ok(R) || !out_dev) return FR_ERR_INVALID_ARG;
+    if (w_lo && !w) return FR_ERR_INVALID_ARG;
+    const int64_t n = R->nx * R->ny;
+    if (!ws_ok(ws, ws_bytes, n)) return FR_ERR_WORKSPACE;
+    const Layout L = layout(n);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > kMassBlocks) blocks = kMassBlocks;
+    const uint8_t* rb = R->kind == FR_ROUTING_D8 ? R->dir : R->mask;
+    return cuda_status(launch_mass_balance(R->kind, R->nx, R->ny, rb, rain, w, w_lo, area,
+                                           reinterpret_cast<double*>((char*)ws + L.partials),
+                                           (int)blocks, out_dev, (cudaStream_t)stream));
+}
+
+size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_t kind,
+                               uint32_t flags) {
+    (void)tiles_host;
+    (void)ntiles;
+    (void)kind;
+    (void)flags;
+    return 0;
+}
+
+fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
+                         int32_t kind, double p, uint32_t flags, void* ws, size_t ws_bytes,
+                         void* stream) {
+    (void)tiles_host;
+    (void)tiles_dev;
+    (void)ntiles;
+    (void)kind;
+    (void)p;
+    (void)flags;
+    (void)ws;
+    (void)ws_bytes;
+    (void)stream;
+    return FR_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

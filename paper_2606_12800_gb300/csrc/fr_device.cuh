@@ -1,0 +1,148 @@
+// fr_device.cuh -- device helpers shared by the flow-routing kernels.
+//
+// Neighbour codes follow the scan order E N W S NE NW SW SE (codes 0..7); the
+// opposite of code k is k ^ 2.  Receiver rules are those of the paper's local
+// flow routing (Sec. 2.1 for D8, App. A for the multi-receiver split) with the
+// arithmetic fixed here so that every kernel that recomputes them gets the
+// same bits.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fr {
+
+constexpr uint8_t kSink = 0xFF;
+constexpr uint32_t kEdgeRoute = 0x1u;
+constexpr uint32_t kD8Lowest = 0x2u;
+
+__host__ __device__ __forceinline__ constexpr int offx(int k) {
+    return (k == 0 || k == 4 || k == 7) ? 1 : (k == 2 || k == 5 || k == 6) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int offy(int k) {
+    return (k == 1 || k == 4 || k == 5) ? -1 : (k == 3 || k == 6 || k == 7) ? 1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp(int k) { return k ^ 2; }
+
+// ---------------------------------------------------------------- two-float
+// Unevaluated sum hi + lo with |lo| <= ulp(hi)/2 (Dekker / Knuth).  The _rn
+// intrinsics keep the compiler from contracting or reassociating.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float a) { return {a, 0.0f}; }
+
+__device__ __forceinline__ df df_norm(float s, float e) {
+    float hi = __fadd_rn(s, e);
+    float lo = __fsub_rn(e, __fsub_rn(hi, s));
+    return {hi, lo};
+}
+
+// Knuth's two-sum of the leading words plus the trailing words.
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return df_norm(s, e);
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+
+// ------------------------------------------------------------ D8 predicate
+// zn[k] = elevation of neighbour k, +inf where the neighbour lies outside the
+// grid (never strictly lower).  Strictly lower neighbours only; the largest
+// fl32(fl32(zc - zk) * c_k) wins, first in scan order on ties.
+__device__ __forceinline__ uint8_t d8_code(float zc, const float (&zn)[8], float c_orth,
+                                           float c_diag, bool lowest) {
+    float best = -1.0f;
+    uint8_t code = kSink;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        float z = zn[k];
+        if (z < zc) {
+            float drop = __fsub_rn(zc, z);
+            float s = lowest ? drop : __fmul_rn(drop, k < 4 ? c_orth : c_diag);
+            if (s > best) {
+                best = s;
+                code = (uint8_t)k;
+            }
+        }
+    }
+    return code;
+}
+
+// ------------------------------------------------------------ MFD weights
+// Reciprocal distances 1/d_k as two-float, set on the host from FP64.
+struct MfdConst {
+    float co_hi, co_lo;  // 1/dx
+    float cd_hi, cd_lo;  // 1/(sqrt(2) dx)
+    float p;
+};
+
+// u_k = s_k^p for a strictly lower neighbour, s_k = (zc - zn)/d_k.  The drop
+// and the product with 1/d are carried as two-float and the trailing word is
+// applied as a first-order correction of the power: (s+e)^p ~ s^p (1 + p e/s).
+__device__ __forceinline__ float mfd_u(float zc, float zn, int k, const MfdConst& m) {
+    float dz = __fsub_rn(zc, zn);
+    float bb = __fsub_rn(dz, zc);
+    float dze = __fadd_rn(__fsub_rn(zc, __fsub_rn(dz, bb)), __fsub_rn(-zn, bb));
+    float ch = k < 4 ? m.co_hi : m.cd_hi;
+    float cl = k < 4 ? m.co_lo : m.cd_lo;
+    float s = __fmul_rn(dz, ch);
+    float se = __fmaf_rn(dz, ch, -s);
+    se = __fmaf_rn(dz, cl, se);
+    se = __fmaf_rn(dze, ch, se);
+    float u = powf(s, m.p);
+    float corr = __fmul_rn(m.p, __fdiv_rn(se, s));
+    return __fmaf_rn(u, corr, u);
+}
+
+// Out-of-line copy of mfd_u for loops that would otherwise replicate powf.
+static __device__ __noinline__ float mfd_u_call(float zc, float zn, int k, MfdConst m) {
+    return mfd_u(zc, zn, k, m);
+}
+
+// Two-float reciprocal of the normaliser S = sum of u_k.
+__device__ __forceinline__ df df_recip(df s) {
+    float r = __frcp_rn(s.hi);
+    float e = __fmaf_rn(-s.hi, r, 1.0f);
+    e = __fmaf_rn(-s.lo, r, e);
+    return df_norm(r, __fmul_rn(r, e));
+}
+
+// Fraction u * (1/S) as two-float.
+__device__ __forceinline__ df mfd_frac(float u, df inv_s) {
+    float p = __fmul_rn(u, inv_s.hi);
+    float e = __fmaf_rn(u, inv_s.hi, -p);
+    e = __fmaf_rn(u, inv_s.lo, e);
+    return df_norm(p, e);
+}
+
+// ------------------------------------------------------------ byte counters
+// Four 8-bit counters per 32-bit word; atomics add n << 8*(i & 3).  Counts
+// never exceed 8, so no carry crosses into a neighbouring byte.
+__device__ __forceinline__ uint32_t counter_add(uint32_t* words, int64_t i, uint32_t n) {
+    uint32_t sh = 8u * (uint32_t)(i & 3);
+    uint32_t old = atomicAdd(words + (i >> 2), n << sh);
+    return ((old >> sh) & 0xFFu) + n;
+}
+
+__device__ __forceinline__ bool is_edge(int64_t x, int64_t y, int64_t nx, int64_t ny) {
+    return x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+}
+
+// Loads that bypass L1: values published by other CTAs after a fence.
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ld_cg(const uint64_t* p) {
+    return (uint64_t)__ldcg((const unsigned long long*)p);
+}
+
+}  // namespace fr

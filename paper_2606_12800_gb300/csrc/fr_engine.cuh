@@ -1,0 +1,596 @@
+// fr_engine.cuh -- exact accumulation over a routing DAG on a DEM grid.
+//
+// Global flow routing solves A w = r with A = I - W (paper Sec. 2.2); the
+// adjoint solves A^T g = gbar.  Both are triangular once cells are processed
+// in dependency order (Sec. 2.4), which is what the sequential high-to-low
+// algorithm does (Sec. 2.1).  On the GPU the grid is cut into CTA tiles that
+// play the role of the paper's per-process subdomains (Sec. 2.4, "each
+// process can solve its linear system independently"):
+//
+//  1. local phase (shared memory): every tile cell whose dependencies all lie
+//     inside the tile -- and recursively inside -- is solved exactly by a
+//     level-synchronous wavefront over the tile's DAG (a topological order;
+//     Sec. 3.2 shows any such order gives the same result).  The frontier is a
+//     shared-memory queue appended with warp-aggregated atomics.  Cells with a
+//     dependency outside the tile (and everything they feed inside it) are
+//     marked "global".
+//  2. global phase: instead of the paper's Richardson iteration across
+//     subdomain boundaries (App. B.1), cross-tile dependencies are resolved
+//     exactly and without waiting: every cell has an arrival counter, each
+//     finished dependency increments it, and the thread that brings it to the
+//     cell's dependency count computes the cell ("last arriver continues") and
+//     walks on downstream.  Work is O(N) and no thread ever waits on another,
+//     so a routing graph with a cycle cannot hang the kernel: its cells are
+//     simply never reached, which the completion count reports.
+//
+// Values are pulled from dependencies in a fixed neighbour order, so results
+// are bit-reproducible.  Real-valued sums are two-float (fp32 hi + lo); unit
+// rain D8 areas are exact integers.
+#pragma once
+
+#include "fr_internal.h"
+
+namespace fr {
+
+template <Mode M, bool W, bool AREA>
+struct Eng {
+    static constexpr bool kMfd = (M == Mode::FwdMfd || M == Mode::AdjMfd);
+    static constexpr bool kAdj = (M == Mode::AdjD8 || M == Mode::AdjMfd);
+    static constexpr bool kVal = W || kAdj || kMfd;      // two-float values are solved
+    static constexpr bool kArea = AREA && (M == Mode::FwdD8);
+    static constexpr bool kBranch = kMfd || kAdj;         // several targets per cell
+    static constexpr int TX = kTileX, TY = kTileY, NC = TX * TY;
+    static constexpr int RX = TX + 2, RY = TY + 2;
+    static constexpr int NT = 256;
+    static constexpr uint8_t kOobRb = kMfd ? 0 : kSink;
+};
+
+// State byte of a tile cell: bits 0-3 in-tile dependencies still missing,
+// bit 4 global, bit 5 solved locally.
+constexpr uint32_t kG = 0x10u, kDone = 0x20u;
+
+template <class E>
+struct alignas(16) Smem {
+    float vhi[E::kVal ? E::NC : 1];
+    float vlo[E::kVal ? E::NC : 1];
+    float ishi[E::kMfd ? E::NC : 1];
+    float islo[E::kMfd ? E::NC : 1];
+    float z[E::kMfd ? E::RX * E::RY : 1];
+    uint32_t area[E::kArea ? E::NC : 1];
+    uint32_t st[E::NC / 4];
+    uint16_t q[E::NC];
+    uint8_t rb[E::RX * E::RY];
+    int qtail;
+    int64_t work;
+    unsigned long long done;
+};
+
+// Receiver mask of a routing byte.  D8 codes above 7 (including FR_SINK) mean
+// no receiver.
+template <bool MFD>
+__device__ __forceinline__ uint32_t recv_mask(uint8_t rb) {
+    if constexpr (MFD) return rb;
+    else return rb < 8 ? (1u << rb) : 0u;
+}
+
+// Neighbour codes of cell (x, y) that lie inside the grid.  Receivers are
+// always masked with it, so routing bytes that point outside the grid (possible
+// in caller-supplied routings) act as "no receiver" instead of reaching outside.
+__device__ __forceinline__ uint32_t grid_mask(int64_t x, int64_t y, int64_t nx, int64_t ny) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        int64_t xn = x + offx(k), yn = y + offy(k);
+        if (xn >= 0 && yn >= 0 && xn < nx && yn < ny) m |= 1u << k;
+    }
+    return m;
+}
+
+// ------------------------------------------------------------ global view
+template <class E>
+__device__ __forceinline__ uint32_t g_recv(const Prob& P, int64_t i) {
+    return recv_mask<E::kMfd>(__ldg(P.rb + i));
+}
+
+// Receivers of cell i restricted to the grid.
+template <class E>
+__device__ __forceinline__ uint32_t g_recv_own(const Prob& P, int64_t i) {
+    int64_t y = i / P.nx, x = i - y * P.nx;
+    return g_recv<E>(P, i) & grid_mask(x, y, P.nx, P.ny);
+}
+
+// Donor mask of cell (x, y) read from the global routing bytes.
+template <class E>
+__device__ __forceinline__ uint32_t g_donors(const Prob& P, int64_t x, int64_t y) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        int64_t xn = x + offx(k), yn = y + offy(k);
+        if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
+        if ((g_recv<E>(P, yn * P.nx + xn) >> opp(k)) & 1u) m |= 1u << k;
+    }
+    return m;
+}
+
+template <class E>
+__device__ __forceinline__ uint32_t g_deps(const Prob& P, int64_t i) {
+    int64_t y = i / P.nx, x = i - y * P.nx;
+    if constexpr (E::kAdj) return g_recv_own<E>(P, i);
+    else return g_donors<E>(P, x, y);
+}
+
+template <class E>
+__device__ __forceinline__ uint32_t g_targets(const Prob& P, int64_t i) {
+    int64_t y = i / P.nx, x = i - y * P.nx;
+    if constexpr (E::kAdj) return g_donors<E>(P, x, y);
+    else return g_recv_own<E>(P, i);
+}
+
+// Inverse normaliser 1/S of cell i's own outflow (MFD), from global memory.
+template <class E>
+__device__ __noinline__ df g_inv_norm(const Prob& P, int64_t i) {
+    uint32_t m = g_recv_own<E>(P, i);
+    int64_t y = i / P.nx, x = i - y * P.nx;
+    float zc = __ldg(P.z + i);
+    df s = df_make(0.0f);
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k)
+        if ((m >> k) & 1u)
+            s = df_add(s, df_make(mfd_u_call(zc, __ldg(P.z + (y + offy(k)) * P.nx + x + offx(k)), k, P.mc)));
+    return df_recip(s);
+}
+
+// Initial value of a cell: rain (forward) or gbar (adjoint).
+template <class E>
+__device__ __forceinline__ df init_value(const Prob& P, int64_t i, uint32_t recv) {
+    if constexpr (!E::kAdj) {
+        return df_make(P.init ? __ldg(P.init + i) : 1.0f);
+    } else {
+        if (P.init) return df_make(__ldg(P.init + i));
+        if (recv) return df_make(0.0f);
+        float h = __ldg(P.wf + i);
+        float l = P.wf_lo ? __ldg(P.wf_lo + i) : 0.0f;
+        return {__fmul_rn(2.0f, h), __fmul_rn(2.0f, l)};
+    }
+}
+
+template <class E>
+__device__ __forceinline__ df g_value(const Prob& P, int64_t i) {
+    return {ld_cg(P.out_hi + i), ld_cg(P.out_lo + i)};
+}
+
+// Computes and publishes the value of a global-phase cell whose dependencies
+// are all final.
+template <class E>
+__device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
+    const int64_t y = t / P.nx, x = t - y * P.nx;
+    const uint32_t recv = g_recv_own<E>(P, t);
+    if constexpr (E::kVal) {
+        df v = init_value<E>(P, t, recv);
+        if constexpr (E::kAdj) {
+            df inv;
+            float zc = 0.0f;
+            if constexpr (E::kMfd) {
+                inv = g_inv_norm<E>(P, t);
+                zc = __ldg(P.z + t);
+            }
+#pragma unroll 1
+            for (int k = 0; k < 8; ++k) {
+                if (!((recv >> k) & 1u)) continue;
+                int64_t j = t + offy(k) * P.nx + offx(k);
+                df gj = g_value<E>(P, j);
+                if constexpr (E::kMfd) gj = df_mul(mfd_frac(mfd_u_call(zc, __ldg(P.z + j), k, P.mc), inv), gj);
+                v = df_add(v, gj);
+            }
+        } else {
+            float zc = E::kMfd ? __ldg(P.z + t) : 0.0f;
+#pragma unroll 1
+            for (int k = 0; k < 8; ++k) {
+                int64_t xn = x + offx(k), yn = y + offy(k);
+                if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
+                int64_t j = yn * P.nx + xn;
+                if (!((g_recv<E>(P, j) >> opp(k)) & 1u)) continue;
+                df wj = g_value<E>(P, j);
+                if constexpr (E::kMfd)
+                    wj = df_mul(mfd_frac(mfd_u_call(__ldg(P.z + j), zc, opp(k), P.mc), g_inv_norm<E>(P, j)), wj);
+                v = df_add(v, wj);
+            }
+        }
+        if (P.out_hi) P.out_hi[t] = v.hi;
+        P.out_lo[t] = v.lo;
+    }
+    if constexpr (E::kArea) {
+        uint64_t a = 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int64_t xn = x + offx(k), yn = y + offy(k);
+            if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
+            int64_t j = yn * P.nx + xn;
+            if (__ldg(P.rb + j) == (uint8_t)opp(k)) a += ld_cg(P.area + j);
+        }
+        P.area[t] = a;
+    }
+}
+
+constexpr int kStack = 8;
+constexpr unsigned kStatusNoProgress = 5u;
+
+// Walks downstream (forward) or upstream (adjoint) from a ready cell.  Cells
+// that become ready along the way are continued by this thread: one directly,
+// further ones on a small private stack that spills into a linked list threaded
+// through P.link (each cell becomes ready exactly once, so every cell owns its
+// link slot and nothing needs clearing).  Returns the number of cells computed.
+template <class E>
+__device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t start) {
+    unsigned long long n = 0;
+    int64_t stack[E::kBranch ? kStack : 1];
+    int sp = 0;
+    int64_t spill = -1;  // head of the spilled list
+    int64_t cur = start;
+    while (true) {
+        walker_compute<E>(P, cur);
+        ++n;
+        __threadfence();
+        const uint32_t tm = g_targets<E>(P, cur);
+        int64_t next = -1;
+        const int64_t y = cur / P.nx, x = cur - y * P.nx;
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            if (!((tm >> k) & 1u)) continue;
+            int64_t t = (y + offy(k)) * P.nx + (x + offx(k));
+            uint32_t got = counter_add(P.cnt, t, 1u);
+            if (got != (uint32_t)__popc(g_deps<E>(P, t))) continue;
+            if (next < 0) {
+                next = t;
+            } else if constexpr (E::kBranch) {
+                if (sp < kStack) {
+                    stack[sp++] = t;
+                } else {
+                    P.link[t] = spill;
+                    spill = t;
+                }
+            }
+        }
+        if (next >= 0) {
+            cur = next;
+            continue;
+        }
+        if constexpr (E::kBranch) {
+            if (sp > 0) {
+                cur = stack[--sp];
+                continue;
+            }
+            if (spill >= 0) {
+                cur = spill;
+                spill = P.link[cur];
+                continue;
+            }
+        }
+        break;
+    }
+    return n;
+}
+
+// Arrival of n finished dependencies at cell u; starts a walker if complete.
+template <class E>
+__device__ __forceinline__ unsigned long long arrive(const Prob& P, int64_t u, uint32_t n) {
+    uint32_t got = counter_add(P.cnt, u, n);
+    if (got == (uint32_t)__popc(g_deps<E>(P, u))) return run_walker<E>(P, u);
+    return 0;
+}
+
+__device__ __forceinline__ uint32_t st_get(const uint32_t* st, int c) {
+    return (st[c >> 2] >> (8 * (c & 3))) & 0xFFu;
+}
+
+// In-tile neighbour mask of tile cell (lx, ly) in a tile of tw x th cells.
+__device__ __forceinline__ uint32_t intile_mask(int lx, int ly, int tw, int th) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        int xn = lx + offx(k), yn = ly + offy(k);
+        if (xn >= 0 && yn >= 0 && xn < tw && yn < th) m |= 1u << k;
+    }
+    return m;
+}
+
+template <class E>
+__device__ __forceinline__ uint32_t s_donors(const Smem<E>& S, int lx, int ly) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if ((recv_mask<E::kMfd>(S.rb[(ly + 1 + offy(k)) * E::RX + (lx + 1 + offx(k))]) >> opp(k)) & 1u)
+            m |= 1u << k;
+    return m;
+}
+
+// Receivers of tile cell (lx, ly); gm is the cell's grid mask.
+template <class E>
+__device__ __forceinline__ uint32_t s_recv(const Smem<E>& S, int lx, int ly, uint32_t gm) {
+    return recv_mask<E::kMfd>(S.rb[(ly + 1) * E::RX + (lx + 1)]) & gm;
+}
+
+template <class E>
+__device__ __forceinline__ uint32_t s_deps(const Smem<E>& S, int lx, int ly, uint32_t gm) {
+    if constexpr (E::kAdj) return s_recv<E>(S, lx, ly, gm);
+    else return s_donors<E>(S, lx, ly);
+}
+
+template <class E>
+__device__ __forceinline__ uint32_t s_targets(const Smem<E>& S, int lx, int ly, uint32_t gm) {
+    if constexpr (E::kAdj) return s_donors<E>(S, lx, ly);
+    else return s_recv<E>(S, lx, ly, gm);
+}
+
+// Warp-aggregated append of tile cell t to the wavefront queue (all 32 lanes
+// must call it together).
+template <class E>
+__device__ __forceinline__ void q_push(Smem<E>& S, bool push, int t) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned b = __ballot_sync(0xffffffffu, push);
+    if (!b) return;
+    int base = 0;
+    if (lane == (unsigned)(__ffs(b) - 1)) base = atomicAdd(&S.qtail, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+    if (push) S.q[base + __popc(b & ((1u << lane) - 1u))] = (uint16_t)t;
+}
+
+// Solves one tile: local phase, publication, cross-tile arrivals.
+template <class E>
+__device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty, Smem<E>& S) {
+    constexpr int TX = E::TX, NC = E::NC, RX = E::RX, RY = E::RY, NT = E::NT;
+    const int tid = threadIdx.x;
+    const int64_t x0 = tx * TX, y0 = ty * E::TY;
+    const int tw = (int)(P.nx - x0 < TX ? P.nx - x0 : TX);
+    const int th = (int)(P.ny - y0 < E::TY ? P.ny - y0 : E::TY);
+    unsigned long long done = 0;
+
+    // routing bytes (and elevations) of the tile plus a one-cell ring
+    for (int i = tid; i < RX * RY; i += NT) {
+        int ry = i / RX, rx = i - ry * RX;
+        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
+        bool in = gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny;
+        S.rb[i] = in ? __ldg(P.rb + gy * P.nx + gx) : E::kOobRb;
+        if constexpr (E::kMfd) S.z[i] = in ? __ldg(P.z + gy * P.nx + gx) : __int_as_float(0x7f800000);
+    }
+    if (tid == 0) S.qtail = 0;
+    __syncthreads();
+
+    // per-cell state and initial values
+    uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
+    for (int c = tid; c < NC; c += NT) {
+        int ly = c / TX, lx = c - ly * TX;
+        uint8_t b = 0;
+        if (lx < tw && ly < th) {
+            int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
+            const uint32_t gm = grid_mask(x0 + lx, y0 + ly, P.nx, P.ny);
+            uint32_t dep = s_deps<E>(S, lx, ly, gm);
+            uint32_t in = intile_mask(lx, ly, tw, th);
+            b = (uint8_t)(__popc(dep & in) | ((dep & ~in) ? kG : 0u));
+            uint32_t recv = s_recv<E>(S, lx, ly, gm);
+            if constexpr (E::kVal) {
+                df v = init_value<E>(P, gi, recv);
+                S.vhi[c] = v.hi;
+                S.vlo[c] = v.lo;
+            }
+            if constexpr (E::kArea) S.area[c] = 1u;
+            if constexpr (E::kMfd) {
+                float zc = S.z[(ly + 1) * RX + lx + 1];
+                df s = df_make(0.0f);
+#pragma unroll 1
+                for (int k = 0; k < 8; ++k)
+                    if ((recv >> k) & 1u)
+                        s = df_add(s, df_make(mfd_u_call(zc, S.z[(ly + 1 + offy(k)) * RX + lx + 1 + offx(k)], k, P.mc)));
+                df inv = recv ? df_recip(s) : df_make(0.0f);
+                S.ishi[c] = inv.hi;
+                S.islo[c] = inv.lo;
+            }
+        } else {
+            b = 0x0F;  // never reaches zero: outside the grid
+        }
+        stb[c] = b;
+    }
+    __syncthreads();
+    for (int c = tid; c < NC; c += NT) q_push<E>(S, (stb[c] & 0x0Fu) == 0, c);
+    __syncthreads();
+
+    // level-synchronous wavefront over the tile's DAG
+    int begin = 0;
+    while (true) {
+        const int end = S.qtail;
+        __syncthreads();
+        if (begin == end) break;
+        for (int base = begin; base < end; base += NT) {
+            const int i = base + tid;
+            const bool act = i < end;
+            int c = 0, lx = 0, ly = 0;
+            uint32_t tm = 0;
+            bool glob = false;
+            if (act) {
+                c = S.q[i];
+                ly = c / TX;
+                lx = c - ly * TX;
+                glob = st_get(S.st, c) & kG;
+                uint32_t in = intile_mask(lx, ly, tw, th);
+                tm = s_targets<E>(S, lx, ly, in) & in;
+                if (!glob) {
+                    uint32_t dep = s_deps<E>(S, lx, ly, in);  // all in tile
+                    if constexpr (E::kVal) {
+                        df v = {S.vhi[c], S.vlo[c]};
+                        float zc = 0.0f;
+                        df myinv = df_make(0.0f);
+                        if constexpr (E::kMfd) {
+                            zc = S.z[(ly + 1) * RX + lx + 1];
+                            myinv = {S.ishi[c], S.islo[c]};
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (!((dep >> k) & 1u)) continue;
+                            int j = c + offy(k) * TX + offx(k);
+                            df vj = {S.vhi[j], S.vlo[j]};
+                            if constexpr (E::kMfd) {
+                                float zj = S.z[(ly + 1 + offy(k)) * RX + lx + 1 + offx(k)];
+                                if constexpr (E::kAdj)
+                                    vj = df_mul(mfd_frac(mfd_u_call(zc, zj, k, P.mc), myinv), vj);
+                                else
+                                    vj = df_mul(mfd_frac(mfd_u_call(zj, zc, opp(k), P.mc), df{S.ishi[j], S.islo[j]}), vj);
+                            }
+                            v = df_add(v, vj);
+                        }
+                        S.vhi[c] = v.hi;
+                        S.vlo[c] = v.lo;
+                    }
+                    if constexpr (E::kArea) {
+                        uint32_t a = S.area[c];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            if ((dep >> k) & 1u) a += S.area[c + offy(k) * TX + offx(k)];
+                        S.area[c] = a;
+                    }
+                    atomicOr(&S.st[c >> 2], kDone << (8 * (c & 3)));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                bool push = false;
+                int t = 0;
+                if ((tm >> k) & 1u) {
+                    t = c + offy(k) * TX + offx(k);
+                    uint32_t sh = 8u * (uint32_t)(t & 3);
+                    if (glob) atomicOr(&S.st[t >> 2], kG << sh);
+                    uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
+                    push = ((old >> sh) & 0x0Fu) == 1u;
+                }
+                q_push<E>(S, push, t);
+            }
+        }
+        __syncthreads();
+        begin = end;
+    }
+
+    // publish locally solved cells (row-major, coalesced)
+    for (int c = tid; c < NC; c += NT) {
+        int ly = c / TX, lx = c - ly * TX;
+        if (lx >= tw || ly >= th) continue;
+        uint32_t b = st_get(S.st, c);
+        if (!(b & kDone)) continue;
+        ++done;
+        int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
+        if constexpr (E::kVal) {
+            if (P.out_hi) P.out_hi[gi] = S.vhi[c];
+            bool need_lo = P.lo_full;
+            if (!need_lo) {
+                // a global cell or a cell of another tile will pull this value
+                uint32_t in = intile_mask(lx, ly, tw, th);
+                uint32_t tm = s_targets<E>(S, lx, ly, grid_mask(x0 + lx, y0 + ly, P.nx, P.ny));
+                if (tm & ~in) need_lo = true;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (((tm & in) >> k) & 1u)
+                        if (st_get(S.st, c + offy(k) * TX + offx(k)) & kG) need_lo = true;
+            }
+            if (need_lo) P.out_lo[gi] = S.vlo[c];
+        }
+        if constexpr (E::kArea) P.area[gi] = S.area[c];
+    }
+    __threadfence();
+    __syncthreads();
+
+    // arrivals at global cells of this tile and at cells of neighbouring tiles
+    for (int c = tid; c < NC; c += NT) {
+        int ly = c / TX, lx = c - ly * TX;
+        if (lx >= tw || ly >= th) continue;
+        uint32_t b = st_get(S.st, c);
+        int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
+        uint32_t in = intile_mask(lx, ly, tw, th);
+        const uint32_t gm = grid_mask(x0 + lx, y0 + ly, P.nx, P.ny);
+        if (b & kG) {
+            uint32_t dep = s_deps<E>(S, lx, ly, gm) & in;
+            uint32_t n = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((dep >> k) & 1u) n += !(st_get(S.st, c + offy(k) * TX + offx(k)) & kG);
+            if (n) done += arrive<E>(P, gi, n);
+        } else if (b & kDone) {
+            uint32_t tm = s_targets<E>(S, lx, ly, gm) & ~in;
+#pragma unroll 1
+            for (int k = 0; k < 8; ++k)
+                if ((tm >> k) & 1u)
+                    done += arrive<E>(P, gi + offy(k) * P.nx + offx(k), 1u);
+        }
+    }
+    return done;
+}
+
+// Block-wide sum of per-thread done counts, added once per CTA; the last CTA
+// to finish compares the total with the expected cell count.
+template <class E>
+__device__ void finish_cta(Smem<E>& S, unsigned long long done, EngineGlobals* G,
+                           unsigned long long total_cells) {
+    for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
+    if (threadIdx.x == 0) S.done = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && done) atomicAdd(&S.done, done);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (S.done) atomicAdd(&G->done_cells, S.done);
+        __threadfence();
+        unsigned fin = atomicAdd(&G->finished_ctas, 1u);
+        if (fin == gridDim.x - 1) {
+            __threadfence();
+            unsigned long long got = atomicAdd(&G->done_cells, 0ull);
+            if (got != total_cells) atomicMax(&G->status, kStatusNoProgress);
+        }
+    }
+}
+
+template <Mode M, bool W, bool AREA>
+__global__ void __launch_bounds__(256) k_engine(Prob P, EngineGlobals* G) {
+    using E = Eng<M, W, AREA>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<E>& S = *reinterpret_cast<Smem<E>*>(smem_raw);
+    const int64_t tile = blockIdx.x;
+    const int64_t ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
+    unsigned long long done = process_tile<E>(P, tx, ty, S);
+    finish_cta<E>(S, done, G, (unsigned long long)(P.nx * P.ny));
+}
+
+// Persistent batched form: CTAs claim tiles of any problem from a global
+// counter until all are taken.  tile_prefix[p] is the first tile of problem p.
+template <Mode M, bool W, bool AREA>
+__global__ void __launch_bounds__(256) k_engine_batch(const Prob* __restrict__ probs,
+                                                      const int64_t* __restrict__ tile_prefix,
+                                                      int nprob, int64_t total_tiles,
+                                                      unsigned long long total_cells,
+                                                      EngineGlobals* G) {
+    using E = Eng<M, W, AREA>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<E>& S = *reinterpret_cast<Smem<E>*>(smem_raw);
+    unsigned long long done = 0;
+    while (true) {
+        if (threadIdx.x == 0) S.work = (int64_t)atomicAdd(&G->work_next, 1ull);
+        __syncthreads();
+        const int64_t w = S.work;
+        __syncthreads();
+        if (w >= total_tiles) break;
+        int lo = 0, hi = nprob - 1;  // last p with tile_prefix[p] <= w
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const Prob P = probs[lo];
+        const int64_t lt = w - tile_prefix[lo];
+        const int64_t ty = lt / P.tiles_x, tx = lt - ty * P.tiles_x;
+        done += process_tile<E>(P, tx, ty, S);
+        __syncthreads();
+    }
+    finish_cta<E>(S, done, G, total_cells);
+}
+
+template <Mode M, bool W, bool AREA>
+constexpr size_t engine_smem() {
+    return sizeof(Smem<Eng<M, W, AREA>>);
+}
+
+}  // namespace fr

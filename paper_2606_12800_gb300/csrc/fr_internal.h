@@ -1,0 +1,79 @@
+// fr_internal.h -- host-side interfaces between the translation units of libfr.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fr_device.cuh"
+
+namespace fr {
+
+MfdConst make_mfd_const(double dx, double p);
+
+// Local flow routing (fr_receivers.cu).
+cudaError_t launch_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx,
+                                uint32_t flags, uint8_t* dir, uint8_t* indeg, cudaStream_t s);
+cudaError_t launch_receivers_mfd(const float* z, int64_t nx, int64_t ny, double dx, double p,
+                                 uint32_t flags, uint8_t* mask, float* frac, uint8_t* indeg,
+                                 cudaStream_t s);
+// Counts non-finite elevations into *count (device, zeroed by the caller).
+cudaError_t launch_count_nonfinite(const float* z, int64_t n, unsigned long long* count,
+                                   cudaStream_t s);
+
+// Per-problem description consumed by the tile engine (fr_engine.cuh).
+struct Prob {
+    int64_t nx, ny;
+    const uint8_t* rb;     // routing bytes: D8 codes or MFD masks
+    const float* z;        // MFD elevations (fractions are recomputed)
+    const float* init;     // forward: rain (NULL = unit); adjoint: dL/dw (NULL = sink loss)
+    const float* wf;       // adjoint: forward water (leading word)
+    const float* wf_lo;    // adjoint: forward water (trailing word) or NULL
+    float* out_hi;         // value leading word (w or dL/dr) or NULL
+    float* out_lo;         // value trailing word (user output or workspace)
+    uint64_t* area;        // D8 forward unit-rain areas or NULL
+    uint32_t* cnt;         // packed byte arrival counters, zeroed before the launch
+    int64_t* link;         // per-cell spill links of the walkers (no init needed)
+    MfdConst mc;
+    int32_t lo_full;       // out_lo is a user output: write it for every cell
+    int32_t tiles_x;       // number of CTA tiles along x
+    int64_t tile_base;     // first global work index of this problem (batched)
+};
+
+// Device-wide bookkeeping kept at the start of the workspace; zeroed (with
+// the arrival counters that follow it) before every engine launch.
+struct EngineGlobals {
+    unsigned long long done_cells;   // cells whose value was computed
+    unsigned long long work_next;    // batched: next tile to claim
+    unsigned long long nonfinite;    // FR_CHECK_FINITE: count of NaN/Inf inputs
+    unsigned int finished_ctas;      // CTAs that have left the kernel
+    unsigned int status;             // fr_status of the device-side checks
+    unsigned long long pad[4];
+};
+static_assert(sizeof(EngineGlobals) == 64, "globals block is 64 bytes");
+
+enum class Mode : int { FwdD8 = 0, FwdMfd = 1, AdjD8 = 2, AdjMfd = 3 };
+
+// Tile engine launches (fr_accumulate.cu).
+cudaError_t launch_engine(Mode mode, bool want_w, bool want_area, const Prob& prob,
+                          EngineGlobals* g, cudaStream_t s);
+cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Prob* probs_dev,
+                                const int64_t* tile_prefix_dev, int32_t nprob,
+                                int64_t total_tiles, unsigned long long total_cells,
+                                EngineGlobals* g, int grid, cudaStream_t s);
+cudaError_t launch_mfd_grad_z(const Prob& prob, const float* g_hi, const float* g_lo,
+                              float* dLdz, cudaStream_t s);
+cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t* rb,
+                                const float* rain, const float* w, const float* w_lo,
+                                const uint64_t* area, double* partials, int nblocks,
+                                double* out, cudaStream_t s);
+cudaError_t launch_receivers_batch(int kind, const Prob* probs_dev, const int64_t* tile_prefix_dev,
+                                   int32_t nprob, int64_t total_tiles, uint32_t flags,
+                                   cudaStream_t s);
+
+// Engine tile shape (cells): every launch uses the same tile so that the
+// batched and single-grid paths share counters and queues.
+constexpr int kTileX = 64;
+constexpr int kTileY = 32;
+
+}  // namespace fr

@@ -1,0 +1,226 @@
+// fr_receivers.cu -- local flow routing kernels (paper Sec. 2.1 for D8,
+// App. A for the multi-receiver split).
+//
+// Each CTA stages a (TY+4) x (TX+4) elevation tile (two-cell halo) in shared
+// memory, computes the routing byte of the tile plus a one-cell ring, and from
+// the ring the number of donors of each tile cell.  Outside the grid the tile
+// holds +inf, which is never strictly lower than anything.
+#include <cmath>
+
+#include "fr_internal.h"
+
+namespace fr {
+
+MfdConst make_mfd_const(double dx, double p) {
+    MfdConst m;
+    double co = 1.0 / dx;
+    double cd = 1.0 / (std::sqrt(2.0) * dx);
+    m.co_hi = (float)co;
+    m.co_lo = (float)(co - (double)m.co_hi);
+    m.cd_hi = (float)cd;
+    m.cd_lo = (float)(cd - (double)m.cd_hi);
+    m.p = (float)p;
+    return m;
+}
+
+namespace {
+
+constexpr int RTX = 128;  // receiver tile width (cells)
+constexpr int RTY = 8;    // receiver tile height
+constexpr int RNT = 256;  // threads
+constexpr int HX = RTX + 4, HY = RTY + 4;
+constexpr int RX = RTX + 2, RY = RTY + 2;
+
+__device__ __forceinline__ void load_z_tile(float* zs, const float* __restrict__ z, int64_t nx,
+                                            int64_t ny, int64_t x0, int64_t y0) {
+    const float inf = __int_as_float(0x7f800000);
+    for (int i = threadIdx.x; i < HX * HY; i += RNT) {
+        int ly = i / HX, lx = i - ly * HX;
+        int64_t gx = x0 + lx - 2, gy = y0 + ly - 2;
+        float v = inf;
+        if (gx >= 0 && gy >= 0 && gx < nx && gy < ny) v = __ldg(z + gy * nx + gx);
+        zs[i] = v;
+    }
+}
+
+// Neighbour elevations of ring-tile cell (rx, ry) (ring coordinates: tile
+// cell (0,0) is (1,1)).
+__device__ __forceinline__ void gather8(const float* zs, int rx, int ry, float (&zn)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) zn[k] = zs[(ry + 1 + offy(k)) * HX + (rx + 1 + offx(k))];
+}
+
+__device__ __forceinline__ void tile_origin(int64_t nx, int64_t& x0, int64_t& y0) {
+    const int64_t tiles_x = (nx + RTX - 1) / RTX;
+    const int64_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    x0 = tx * RTX;
+    y0 = ty * RTY;
+}
+
+template <bool INDEG>
+__global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ z, int64_t nx,
+                                                      int64_t ny, float c_orth, float c_diag,
+                                                      uint32_t flags, uint8_t* __restrict__ dir,
+                                                      uint8_t* __restrict__ indeg) {
+    __shared__ float zs[HX * HY];
+    __shared__ uint8_t ds[RX * RY];
+    int64_t x0, y0;
+    tile_origin(nx, x0, y0);
+    load_z_tile(zs, z, nx, ny, x0, y0);
+    __syncthreads();
+    const bool lowest = flags & kD8Lowest;
+    const bool edge_route = flags & kEdgeRoute;
+    // routing byte for the tile (+ ring when donor counts are wanted)
+    const int rx0 = INDEG ? 0 : 1, ry0 = INDEG ? 0 : 1;
+    const int rw = INDEG ? RX : RTX, rh = INDEG ? RY : RTY;
+    for (int i = threadIdx.x; i < rw * rh; i += RNT) {
+        int ry = ry0 + i / rw, rx = rx0 + i % rw;
+        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
+        uint8_t code = kSink;
+        if (gx >= 0 && gy >= 0 && gx < nx && gy < ny &&
+            (edge_route || !is_edge(gx, gy, nx, ny))) {
+            float zn[8];
+            gather8(zs, rx, ry, zn);
+            code = d8_code(zs[(ry + 1) * HX + (rx + 1)], zn, c_orth, c_diag, lowest);
+        }
+        ds[ry * RX + rx] = code;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RTX * RTY; i += RNT) {
+        int ly = i / RTX, lx = i - ly * RTX;
+        int64_t gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        int64_t gi = gy * nx + gx;
+        dir[gi] = ds[(ly + 1) * RX + lx + 1];
+        if (INDEG) {
+            int n = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                n += ds[(ly + 1 + offy(k)) * RX + (lx + 1 + offx(k))] == (uint8_t)opp(k);
+            indeg[gi] = (uint8_t)n;
+        }
+    }
+}
+
+template <bool FRAC, bool INDEG>
+__global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__ z, int64_t nx,
+                                                       int64_t ny, MfdConst mc, uint32_t flags,
+                                                       uint8_t* __restrict__ mask,
+                                                       float* __restrict__ frac,
+                                                       uint8_t* __restrict__ indeg) {
+    __shared__ float zs[HX * HY];
+    __shared__ uint8_t ms[RX * RY];
+    int64_t x0, y0;
+    tile_origin(nx, x0, y0);
+    load_z_tile(zs, z, nx, ny, x0, y0);
+    __syncthreads();
+    const bool edge_route = flags & kEdgeRoute;
+    const int rx0 = INDEG ? 0 : 1, ry0 = INDEG ? 0 : 1;
+    const int rw = INDEG ? RX : RTX, rh = INDEG ? RY : RTY;
+    for (int i = threadIdx.x; i < rw * rh; i += RNT) {
+        int ry = ry0 + i / rw, rx = rx0 + i % rw;
+        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
+        uint8_t m = 0;
+        if (gx >= 0 && gy >= 0 && gx < nx && gy < ny &&
+            (edge_route || !is_edge(gx, gy, nx, ny))) {
+            float zc = zs[(ry + 1) * HX + (rx + 1)];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (zs[(ry + 1 + offy(k)) * HX + (rx + 1 + offx(k))] < zc) m |= (uint8_t)(1u << k);
+        }
+        ms[ry * RX + rx] = m;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RTX * RTY; i += RNT) {
+        int ly = i / RTX, lx = i - ly * RTX;
+        int64_t gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        int64_t gi = gy * nx + gx;
+        uint8_t m = ms[(ly + 1) * RX + lx + 1];
+        mask[gi] = m;
+        if (FRAC) {
+            float zc = zs[(ly + 2) * HX + (lx + 2)];
+            float u[8];
+            df s = df_make(0.0f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                u[k] = 0.0f;
+                if (m & (1u << k)) {
+                    u[k] = mfd_u(zc, zs[(ly + 2 + offy(k)) * HX + (lx + 2 + offx(k))], k, mc);
+                    s = df_add(s, df_make(u[k]));
+                }
+            }
+            float f[8];
+            if (m) {
+                df inv = df_recip(s);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k] = (m & (1u << k)) ? mfd_frac(u[k], inv).hi : 0.0f;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k] = 0.0f;
+            }
+            float4* fo = reinterpret_cast<float4*>(frac + gi * 8);
+            fo[0] = make_float4(f[0], f[1], f[2], f[3]);
+            fo[1] = make_float4(f[4], f[5], f[6], f[7]);
+        }
+        if (INDEG) {
+            int n = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                n += (ms[(ly + 1 + offy(k)) * RX + (lx + 1 + offx(k))] >> opp(k)) & 1;
+            indeg[gi] = (uint8_t)n;
+        }
+    }
+}
+
+__global__ void k_count_nonfinite(const float* __restrict__ z, int64_t n,
+                                  unsigned long long* count) {
+    unsigned long long local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        local += !isfinite(z[i]);
+    for (int o = 16; o; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+}  // namespace
+
+cudaError_t launch_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx,
+                                uint32_t flags, uint8_t* dir, uint8_t* indeg, cudaStream_t s) {
+    const unsigned grid = (unsigned)(((nx + RTX - 1) / RTX) * ((ny + RTY - 1) / RTY));
+    float co = (float)(1.0 / dx);
+    float cd = (float)(1.0 / (std::sqrt(2.0) * dx));
+    if (indeg)
+        k_receivers_d8<true><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, indeg);
+    else
+        k_receivers_d8<false><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_receivers_mfd(const float* z, int64_t nx, int64_t ny, double dx, double p,
+                                 uint32_t flags, uint8_t* mask, float* frac, uint8_t* indeg,
+                                 cudaStream_t s) {
+    const unsigned grid = (unsigned)(((nx + RTX - 1) / RTX) * ((ny + RTY - 1) / RTY));
+    MfdConst mc = make_mfd_const(dx, p);
+    if (frac && indeg)
+        k_receivers_mfd<true, true><<<grid, RNT, 0, s>>>(z, nx, ny, mc, flags, mask, frac, indeg);
+    else if (frac)
+        k_receivers_mfd<true, false><<<grid, RNT, 0, s>>>(z, nx, ny, mc, flags, mask, frac, nullptr);
+    else if (indeg)
+        k_receivers_mfd<false, true><<<grid, RNT, 0, s>>>(z, nx, ny, mc, flags, mask, nullptr, indeg);
+    else
+        k_receivers_mfd<false, false><<<grid, RNT, 0, s>>>(z, nx, ny, mc, flags, mask, nullptr,
+                                                           nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_nonfinite(const float* z, int64_t n, unsigned long long* count,
+                                   cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_count_nonfinite<<<(unsigned)blocks, 256, 0, s>>>(z, n, count);
+    return cudaGetLastError();
+}
+
+}  // namespace fr

@@ -1,0 +1,81 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/fr.h declares, and rejects bad arguments synchronously."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2606_12800_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "fr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_lib.EXPORTS)
+
+
+def test_status_strings_and_version(lib):
+    for code in range(7):
+        assert lib.fr_status_string(code)
+    assert lib.fr_version() >= 100
+
+
+def test_workspace_size(lib):
+    assert lib.fr_workspace_size(_lib.FR_OP_RECEIVERS, 10, 10, 0) == 0
+    n = lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 4096, 4096, 0)
+    assert n >= 4096 * 4096 * 13
+    assert n % 256 == 0
+    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 0, 10, 0) == 0
+    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 10, 10, 0x80) == 0
+    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 1 << 21, 1 << 21, 0) == 0  # > 2^40 cells
+
+
+def test_argument_validation_is_synchronous(lib):
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    # null DEM / output, bad sizes, bad dx, unknown flags: rejected before any CUDA call
+    assert lib.fr_receivers_d8(None, 4, 4, 1.0, 0, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_d8(fake, 0, 4, 1.0, 0, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_d8(fake, 4, 4, -1.0, 0, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_d8(fake, 4, 4, float("nan"), 0, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_d8(fake, 4, 4, 1.0, 0x100, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 0.0, 0, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
+    R = _lib.fr_routing()
+    R.kind = 7
+    R.nx = R.ny = 4
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+    R.kind = _lib.FR_ROUTING_D8
+    R.dir = 0x1000
+    # no output requested
+    assert lib.fr_accumulate(ctypes.byref(R), None, None, None, None, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+    # workspace missing / too small / misaligned
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, None, 0, None) == _lib.FR_ERR_WORKSPACE
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, fake, 16, None) == _lib.FR_ERR_WORKSPACE
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, P(0x1001), 1 << 20, None) == _lib.FR_ERR_WORKSPACE
+    # MFD: area output is D8-only; dL/dz is MFD-only
+    R.kind = _lib.FR_ROUTING_MFD
+    R.mask = 0x1000
+    R.dem = 0x1000
+    R.dx = 30.0
+    R.p = 1.1
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+    R.kind = _lib.FR_ROUTING_D8
+    assert lib.fr_route_adjoint(ctypes.byref(R), fake, None, None, fake, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+    R.reserved = 1
+    assert lib.fr_mass_balance(ctypes.byref(R), None, fake, None, None, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (stated per test): D8 receiver codes, donor counts, MFD masks and unit-rain
+areas bit-exact; real-valued water within 1e-6 relative of the FP64 oracle per
+cell (the fp32 two-float leading word); the two-float pair within 1e-10 for D8.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_12800_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_W = 1e-6
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_12800_gb300 import api as a
+    return a
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(got, ref):
+    ref = np.asarray(ref, np.float64)
+    got = np.asarray(got, np.float64)
+    den = np.where(ref == 0, 1.0, np.abs(ref))
+    return np.max(np.abs(got - ref) / den) if ref.size else 0.0
+
+
+SHAPES = [(1, 1), (1, 7), (9, 1), (3, 3), (33, 65), (64, 32), (65, 33), (97, 131), (256, 256),
+          (300, 517)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE, oracle.D8_LOWEST,
+                                   oracle.EDGE_ROUTE | oracle.D8_LOWEST])
+def test_receivers_d8_bit_exact(api, shape, flags):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, seed=ny * 7 + nx)
+    d, n = api.receivers_d8(cuda(z), 30.0, flags, indeg=True)
+    d_ref = oracle.receivers_d8(z, 30.0, flags)
+    np.testing.assert_array_equal(d.cpu().numpy(), d_ref)
+    np.testing.assert_array_equal(n.cpu().numpy(), oracle.indegree(d_ref, False))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE])
+def test_route_d8_parity(api, shape, flags):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, seed=ny * 3 + nx)
+    rain = inputs.rain_field(ny, nx, 5)
+    out = api.route_d8(cuda(z), 30.0, cuda(rain), flags, want_w=True, want_lo=True,
+                       want_area=True, want_dir=True)
+    d_ref, w_ref, _, order = oracle.route_d8(z, 30.0, rain, flags)
+    _, a_ref = oracle.accumulate_d8(d_ref, order, None)
+    np.testing.assert_array_equal(out["dir"].cpu().numpy(), d_ref)
+    np.testing.assert_array_equal(out["area"].cpu().numpy().astype(np.uint64), a_ref)
+    w = out["w"].cpu().numpy()
+    lo = out["w_lo"].cpu().numpy()
+    assert relerr(w, w_ref) <= RTOL_W
+    assert relerr(w.astype(np.float64) + lo, w_ref) <= 1e-10
+    assert api.get_status() == 0
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (300, 517), (5, 700)])
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE, oracle.D8_LOWEST])
+def test_planar_deep_chains(api, shape, flags):
+    """Plane toward +x: every row is one long chain crossing many tiles, so
+    almost every cell is reached by the cross-tile walkers."""
+    ny, nx = shape
+    z = inputs.planar_dem(ny, nx, 0.01, 30.0)
+    out = api.route_d8(cuda(z), 30.0, None, flags, want_w=True, want_area=True)
+    _, w_ref, a_ref, _ = oracle.route_d8(z, 30.0, None, flags)
+    np.testing.assert_array_equal(out["area"].cpu().numpy().astype(np.uint64), a_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    assert api.get_status() == 0
+
+
+def test_unit_rain_only_and_determinism(api):
+    z = inputs.fractal_dem(700, 900, seed=11)
+    zt = cuda(z)
+    a1 = api.route_d8(zt, 30.0, None, 0, want_w=False, want_area=True)["area"]
+    a2 = api.route_d8(zt, 30.0, None, 0, want_w=False, want_area=True)["area"]
+    assert torch.equal(a1, a2)
+    rain = cuda(inputs.rain_field(700, 900, 11))
+    w1 = api.route_d8(zt, 30.0, rain, 0, want_w=True, want_lo=True, want_area=False)
+    w2 = api.route_d8(zt, 30.0, rain, 0, want_w=True, want_lo=True, want_area=False)
+    assert torch.equal(w1["w"], w2["w"]) and torch.equal(w1["w_lo"], w2["w_lo"])
+    _, _, a_ref, _ = oracle.route_d8(z, 30.0)
+    np.testing.assert_array_equal(a1.cpu().numpy().astype(np.uint64), a_ref)
+
+
+@pytest.mark.parametrize("shape", [(1, 9), (3, 3), (33, 65), (97, 131), (256, 256), (300, 517)])
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE])
+def test_receivers_mfd(api, shape, flags):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=ny + nx)
+    m, f, n = api.receivers_mfd(cuda(z), 30.0, 1.1, flags, frac=True, indeg=True)
+    m_ref, f_ref = oracle.receivers_mfd(z, 30.0, 1.1, flags)
+    np.testing.assert_array_equal(m.cpu().numpy(), m_ref)
+    np.testing.assert_array_equal(n.cpu().numpy(), oracle.indegree(m_ref, True))
+    f = f.cpu().numpy().astype(np.float64)
+    assert np.all((f == 0) == (f_ref == 0))
+    nz = f_ref > 0
+    assert np.max(np.abs(f[nz] - f_ref[nz]) / f_ref[nz]) <= 2e-6
+
+
+@pytest.mark.parametrize("shape", [(1, 9), (33, 65), (97, 131), (256, 256), (300, 517)])
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE])
+def test_route_mfd_parity(api, shape, flags):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=2 * ny + nx)
+    rain = inputs.rain_field(ny, nx, 3)
+    out = api.route_mfd(cuda(z), 30.0, 1.1, cuda(rain), flags, want_lo=True, want_mask=True)
+    m_ref, f_ref, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, rain, flags)
+    np.testing.assert_array_equal(out["mask"].cpu().numpy(), m_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    assert api.get_status() == 0
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (256, 256), (300, 517)])
+def test_adjoint_d8(api, shape):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, seed=nx)
+    rain = inputs.rain_field(ny, nx, 1)
+    out = api.route_d8(cuda(z), 30.0, cuda(rain), 0, want_w=True, want_lo=True, want_dir=True,
+                       want_area=False)
+    R = api.routing_d8(out["dir"])
+    dLdr, _ = api.adjoint(R, out["w"], out["w_lo"])
+    d_ref, w_ref, _, order = oracle.route_d8(z, 30.0, rain)
+    g_ref = oracle.adjoint(order, w_ref, dir_=d_ref)
+    assert relerr(dLdr.cpu().numpy(), g_ref) <= RTOL_W
+    # arbitrary incoming gradient
+    gbar = np.random.default_rng(0).random((ny, nx), dtype=np.float32)
+    dLdr, _ = api.adjoint(R, out["w"], out["w_lo"], dLdw=cuda(gbar))
+    g_ref = oracle.adjoint(order, w_ref, dir_=d_ref, gbar=gbar.astype(np.float64))
+    assert relerr(dLdr.cpu().numpy(), g_ref) <= RTOL_W
+    assert api.get_status() == 0
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (256, 256), (300, 517)])
+def test_adjoint_mfd(api, shape):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=nx + 1)
+    rain = inputs.rain_field(ny, nx, 2)
+    zt = cuda(z)
+    m = api.receivers_mfd(zt, 30.0, 1.1)
+    R = api.routing_mfd(m, zt, 30.0, 1.1)
+    o = api.accumulate(R, cuda(rain), want_w=True, want_lo=True)
+    dLdr, dLdz = api.adjoint(R, o["w"], o["w_lo"], want_dz=True)
+    m_ref, f_ref, w_ref, order = oracle.route_mfd(z, 30.0, 1.1, rain)
+    g_ref = oracle.adjoint(order, w_ref, frac=f_ref)
+    dz_ref = oracle.mfd_grad_z(z, 30.0, 1.1, f_ref, w_ref, g_ref)
+    assert relerr(dLdr.cpu().numpy(), g_ref) <= RTOL_W
+    dz = dLdz.cpu().numpy().astype(np.float64)
+    scale = np.abs(dz_ref).max()
+    assert np.max(np.abs(dz - dz_ref)) <= 1e-4 * scale
+    big = np.abs(dz_ref) > 1e-2 * scale
+    assert np.max(np.abs(dz[big] - dz_ref[big]) / np.abs(dz_ref[big])) <= 1e-3
+    assert api.get_status() == 0
+
+
+def test_mass_balance(api):
+    ny, nx = 400, 300
+    z = inputs.fractal_dem(ny, nx, seed=4)
+    rain = inputs.rain_field(ny, nx, 4)
+    rt = cuda(rain)
+    out = api.route_d8(cuda(z), 30.0, rt, 0, want_w=True, want_lo=True, want_area=True,
+                       want_dir=True)
+    R = api.routing_d8(out["dir"])
+    mb = api.mass_balance(R, rt, out["w"], out["w_lo"], out["area"]).cpu().numpy()
+    d_ref, w_ref, _, _ = oracle.route_d8(z, 30.0, rain)
+    s_ref, r_ref = oracle.mass_balance(w_ref, rain, dir_=d_ref)
+    assert mb[2] == nx * ny
+    assert abs(mb[1] - r_ref) <= 1e-12 * r_ref
+    assert abs(mb[0] - s_ref) <= 1e-12 * s_ref
+    assert abs(mb[0] - mb[1]) <= 1e-10 * mb[1]
+    mb2 = api.mass_balance(R, rt, out["w"], out["w_lo"], out["area"]).cpu().numpy()
+    assert np.array_equal(mb, mb2)
+
+
+def test_cycle_reports_no_progress(api):
+    """A routing with a cycle (two cells pointing at each other) must finish
+    and leave FR_ERR_NO_PROGRESS in the status word (no hang)."""
+    ny, nx = 40, 70
+    d = np.full((ny, nx), oracle.SINK, np.uint8)
+    d[10, 10] = 0   # E  -> (11, 10)
+    d[10, 11] = 2   # W  -> (10, 10)
+    d[20, 63] = 0   # a cycle across a tile border (x = 63 | 64)
+    d[20, 64] = 2
+    R = api.routing_d8(cuda(d))
+    api.accumulate(R, None, want_w=True, want_area=True)
+    assert api.get_status() == 5
+    # a good routing afterwards on the same workspace is clean again
+    z = inputs.fractal_dem(ny, nx, seed=1)
+    api.route_d8(cuda(z), 30.0)
+    assert api.get_status() == 0
+
+
+def test_routing_pointing_outside_grid_is_a_sink(api):
+    """Caller-supplied codes that point out of the grid act as no receiver."""
+    ny, nx = 16, 16
+    d = np.full((ny, nx), oracle.SINK, np.uint8)
+    d[0, :] = 1    # N from the top row: outside
+    d[:, 0] = 2    # W from the left column: outside
+    d[5, 5] = 0    # E -> (6, 5)
+    R = api.routing_d8(cuda(d))
+    out = api.accumulate(R, None, want_w=True, want_area=True)
+    a = out["area"].cpu().numpy()
+    assert a[5, 6] == 2 and a.sum() == ny * nx + 1
+    assert api.get_status() == 0
