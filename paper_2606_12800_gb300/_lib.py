@@ -12,7 +12,7 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libfr.so")
+LIB_PATH = os.environ.get("FR_LIB_PATH") or os.path.join(_HERE, "_build", "libfr.so")
 
 # status codes (fr_status)
 FR_OK = 0

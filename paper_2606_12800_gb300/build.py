@@ -36,19 +36,24 @@ def _newest_header() -> float:
     return max(os.path.getmtime(h) for h in hdrs)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False) -> str:
+    """Compiles every .cu under csrc/ and links libfr.so.  ``debug_bounds``
+    builds a bounds-checking variant into _build/debug/ instead."""
+    build_dir = os.path.join(BUILD, "debug") if debug_bounds else BUILD
+    lib_path = os.path.join(build_dir, "libfr.so")
+    extra = ["-DFR_DEBUG_BOUNDS"] if debug_bounds else []
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = _newest_header()
     objs, jobs = [], []
     for src in sources:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         stale = (force or not os.path.exists(obj) or os.path.getmtime(obj) < os.path.getmtime(src)
                  or os.path.getmtime(obj) < hdr_time)
         if stale:
-            jobs.append([nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,13 +66,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if (jobs or not os.path.exists(lib_path)
+            or any(os.path.getmtime(o) > os.path.getmtime(lib_path) for o in objs)):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
              "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                debug_bounds="--debug-bounds" in sys.argv))

@@ -281,3 +281,14 @@ cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t*
 }
 
 }  // namespace fr
+
+#ifdef FR_DEBUG_BOUNDS
+// Debug builds only: first out-of-range (site << 48 | index) seen by the
+// engine kernels of this translation unit (0 = none); clears it.
+extern "C" unsigned long long fr_debug_bad_engine(void) {
+    unsigned long long v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, fr::fr_debug_bad, sizeof(v));
+    cudaMemcpyToSymbol(fr::fr_debug_bad, &z, sizeof(z));
+    return v;
+}
+#endif

@@ -16,11 +16,22 @@ constexpr uint8_t kSink = 0xFF;
 constexpr uint32_t kEdgeRoute = 0x1u;
 constexpr uint32_t kD8Lowest = 0x2u;
 
+// Offsets as 2-bit fields (offset + 1) packed per code, decoded with plain
+// signed integer arithmetic (a nested-ternary form of these functions was
+// zero-extended instead of sign-extended in non-unrolled loops).
 __host__ __device__ __forceinline__ constexpr int offx(int k) {
-    return (k == 0 || k == 4 || k == 7) ? 1 : (k == 2 || k == 5 || k == 6) ? -1 : 0;
+    return (int)((33350u >> (2 * k)) & 3u) - 1;  // +1 0 -1 0 +1 -1 -1 +1
 }
 __host__ __device__ __forceinline__ constexpr int offy(int k) {
-    return (k == 1 || k == 4 || k == 5) ? -1 : (k == 3 || k == 6 || k == 7) ? 1 : 0;
+    return (int)((41105u >> (2 * k)) & 3u) - 1;  // 0 -1 0 +1 -1 -1 +1 +1
+}
+static_assert(offx(0) == 1 && offx(1) == 0 && offx(2) == -1 && offx(3) == 0 && offx(4) == 1 &&
+              offx(5) == -1 && offx(6) == -1 && offx(7) == 1, "offx table");
+static_assert(offy(0) == 0 && offy(1) == -1 && offy(2) == 0 && offy(3) == 1 && offy(4) == -1 &&
+              offy(5) == -1 && offy(6) == 1 && offy(7) == 1, "offy table");
+// Linear index offset of code k on a grid with nx columns.
+__host__ __device__ __forceinline__ int64_t offi(int k, int64_t nx) {
+    return (int64_t)offy(k) * nx + (int64_t)offx(k);
 }
 __host__ __device__ __forceinline__ constexpr int opp(int k) { return k ^ 2; }
 
@@ -138,6 +149,23 @@ __device__ __forceinline__ uint32_t counter_add(uint32_t* words, int64_t i, uint
 __device__ __forceinline__ bool is_edge(int64_t x, int64_t y, int64_t nx, int64_t ny) {
     return x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
 }
+
+// ------------------------------------------------------------ debug bounds
+// With -DFR_DEBUG_BOUNDS every engine and receiver memory access is checked;
+// the first out-of-range (site, index) is recorded in fr_debug_bad and the
+// access is skipped.  Release builds compile the checks away.
+#ifdef FR_DEBUG_BOUNDS
+__device__ unsigned long long fr_debug_bad;
+__device__ __forceinline__ bool fr_ok(int64_t i, int64_t n, unsigned site) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&fr_debug_bad, 0ull,
+              ((unsigned long long)site << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull));
+    return false;
+}
+#define FR_OK(i, n, site) ::fr::fr_ok((int64_t)(i), (int64_t)(n), (site))
+#else
+#define FR_OK(i, n, site) true
+#endif
 
 // Loads that bypass L1: values published by other CTAs after a fence.
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }

@@ -80,16 +80,49 @@ __device__ __forceinline__ uint32_t grid_mask(int64_t x, int64_t y, int64_t nx, 
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        int64_t xn = x + offx(k), yn = y + offy(k);
+        int64_t xn = x + (int64_t)offx(k), yn = y + (int64_t)offy(k);
         if (xn >= 0 && yn >= 0 && xn < nx && yn < ny) m |= 1u << k;
     }
     return m;
 }
 
 // ------------------------------------------------------------ global view
+// Accessors of the per-problem arrays (bounds-checked in debug builds).
+__device__ __forceinline__ int64_t ncell(const Prob& P) { return P.nx * P.ny; }
+__device__ __forceinline__ uint8_t rd_rb(const Prob& P, int64_t i) {
+    return FR_OK(i, ncell(P), 1) ? __ldg(P.rb + i) : (uint8_t)0;
+}
+__device__ __forceinline__ float rd_z(const Prob& P, int64_t i) {
+    return FR_OK(i, ncell(P), 2) ? __ldg(P.z + i) : 0.0f;
+}
+__device__ __forceinline__ float rd_in(const float* a, const Prob& P, int64_t i, unsigned site) {
+    return FR_OK(i, ncell(P), site) ? __ldg(a + i) : 0.0f;
+}
+__device__ __forceinline__ void wr_f(float* a, const Prob& P, int64_t i, float v, unsigned site) {
+    if (FR_OK(i, ncell(P), site)) a[i] = v;
+}
+__device__ __forceinline__ float rd_cg(const float* a, const Prob& P, int64_t i, unsigned site) {
+    return FR_OK(i, ncell(P), site) ? ld_cg(a + i) : 0.0f;
+}
+__device__ __forceinline__ uint64_t rd_area(const Prob& P, int64_t i) {
+    return FR_OK(i, ncell(P), 3) ? ld_cg(P.area + i) : 0ull;
+}
+__device__ __forceinline__ void wr_area(const Prob& P, int64_t i, uint64_t v) {
+    if (FR_OK(i, ncell(P), 4)) P.area[i] = v;
+}
+__device__ __forceinline__ uint32_t cnt_add(const Prob& P, int64_t i, uint32_t n) {
+    return FR_OK(i, ncell(P), 5) ? counter_add(P.cnt, i, n) : 0xFFu;
+}
+__device__ __forceinline__ int64_t rd_link(const Prob& P, int64_t i) {
+    return FR_OK(i, ncell(P), 6) ? P.link[i] : -1;
+}
+__device__ __forceinline__ void wr_link(const Prob& P, int64_t i, int64_t v) {
+    if (FR_OK(i, ncell(P), 7)) P.link[i] = v;
+}
+
 template <class E>
 __device__ __forceinline__ uint32_t g_recv(const Prob& P, int64_t i) {
-    return recv_mask<E::kMfd>(__ldg(P.rb + i));
+    return recv_mask<E::kMfd>(rd_rb(P, i));
 }
 
 // Receivers of cell i restricted to the grid.
@@ -105,7 +138,7 @@ __device__ __forceinline__ uint32_t g_donors(const Prob& P, int64_t x, int64_t y
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        int64_t xn = x + offx(k), yn = y + offy(k);
+        int64_t xn = x + (int64_t)offx(k), yn = y + (int64_t)offy(k);
         if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
         if ((g_recv<E>(P, yn * P.nx + xn) >> opp(k)) & 1u) m |= 1u << k;
     }
@@ -131,12 +164,12 @@ template <class E>
 __device__ __noinline__ df g_inv_norm(const Prob& P, int64_t i) {
     uint32_t m = g_recv_own<E>(P, i);
     int64_t y = i / P.nx, x = i - y * P.nx;
-    float zc = __ldg(P.z + i);
+    float zc = rd_z(P, i);
     df s = df_make(0.0f);
 #pragma unroll 1
     for (int k = 0; k < 8; ++k)
         if ((m >> k) & 1u)
-            s = df_add(s, df_make(mfd_u_call(zc, __ldg(P.z + (y + offy(k)) * P.nx + x + offx(k)), k, P.mc)));
+            s = df_add(s, df_make(mfd_u_call(zc, rd_z(P, i + offi(k, P.nx)), k, P.mc)));
     return df_recip(s);
 }
 
@@ -144,19 +177,19 @@ __device__ __noinline__ df g_inv_norm(const Prob& P, int64_t i) {
 template <class E>
 __device__ __forceinline__ df init_value(const Prob& P, int64_t i, uint32_t recv) {
     if constexpr (!E::kAdj) {
-        return df_make(P.init ? __ldg(P.init + i) : 1.0f);
+        return df_make(P.init ? rd_in(P.init, P, i, 8) : 1.0f);
     } else {
-        if (P.init) return df_make(__ldg(P.init + i));
+        if (P.init) return df_make(rd_in(P.init, P, i, 8));
         if (recv) return df_make(0.0f);
-        float h = __ldg(P.wf + i);
-        float l = P.wf_lo ? __ldg(P.wf_lo + i) : 0.0f;
+        float h = rd_in(P.wf, P, i, 9);
+        float l = P.wf_lo ? rd_in(P.wf_lo, P, i, 10) : 0.0f;
         return {__fmul_rn(2.0f, h), __fmul_rn(2.0f, l)};
     }
 }
 
 template <class E>
 __device__ __forceinline__ df g_value(const Prob& P, int64_t i) {
-    return {ld_cg(P.out_hi + i), ld_cg(P.out_lo + i)};
+    return {rd_cg(P.out_hi, P, i, 11), rd_cg(P.out_lo, P, i, 12)};
 }
 
 // Computes and publishes the value of a global-phase cell whose dependencies
@@ -172,43 +205,43 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
             float zc = 0.0f;
             if constexpr (E::kMfd) {
                 inv = g_inv_norm<E>(P, t);
-                zc = __ldg(P.z + t);
+                zc = rd_z(P, t);
             }
 #pragma unroll 1
             for (int k = 0; k < 8; ++k) {
                 if (!((recv >> k) & 1u)) continue;
-                int64_t j = t + offy(k) * P.nx + offx(k);
+                int64_t j = t + offi(k, P.nx);
                 df gj = g_value<E>(P, j);
-                if constexpr (E::kMfd) gj = df_mul(mfd_frac(mfd_u_call(zc, __ldg(P.z + j), k, P.mc), inv), gj);
+                if constexpr (E::kMfd) gj = df_mul(mfd_frac(mfd_u_call(zc, rd_z(P, j), k, P.mc), inv), gj);
                 v = df_add(v, gj);
             }
         } else {
-            float zc = E::kMfd ? __ldg(P.z + t) : 0.0f;
+            float zc = E::kMfd ? rd_z(P, t) : 0.0f;
 #pragma unroll 1
             for (int k = 0; k < 8; ++k) {
-                int64_t xn = x + offx(k), yn = y + offy(k);
+                int64_t xn = x + (int64_t)offx(k), yn = y + (int64_t)offy(k);
                 if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
                 int64_t j = yn * P.nx + xn;
                 if (!((g_recv<E>(P, j) >> opp(k)) & 1u)) continue;
                 df wj = g_value<E>(P, j);
                 if constexpr (E::kMfd)
-                    wj = df_mul(mfd_frac(mfd_u_call(__ldg(P.z + j), zc, opp(k), P.mc), g_inv_norm<E>(P, j)), wj);
+                    wj = df_mul(mfd_frac(mfd_u_call(rd_z(P, j), zc, opp(k), P.mc), g_inv_norm<E>(P, j)), wj);
                 v = df_add(v, wj);
             }
         }
-        if (P.out_hi) P.out_hi[t] = v.hi;
-        P.out_lo[t] = v.lo;
+        if (P.out_hi) wr_f(P.out_hi, P, t, v.hi, 13);
+        wr_f(P.out_lo, P, t, v.lo, 14);
     }
     if constexpr (E::kArea) {
         uint64_t a = 1;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            int64_t xn = x + offx(k), yn = y + offy(k);
+            int64_t xn = x + (int64_t)offx(k), yn = y + (int64_t)offy(k);
             if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
             int64_t j = yn * P.nx + xn;
-            if (__ldg(P.rb + j) == (uint8_t)opp(k)) a += ld_cg(P.area + j);
+            if (rd_rb(P, j) == (uint8_t)opp(k)) a += rd_area(P, j);
         }
-        P.area[t] = a;
+        wr_area(P, t, a);
     }
 }
 
@@ -237,8 +270,8 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
 #pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             if (!((tm >> k) & 1u)) continue;
-            int64_t t = (y + offy(k)) * P.nx + (x + offx(k));
-            uint32_t got = counter_add(P.cnt, t, 1u);
+            int64_t t = cur + offi(k, P.nx);
+            uint32_t got = cnt_add(P, t, 1u);
             if (got != (uint32_t)__popc(g_deps<E>(P, t))) continue;
             if (next < 0) {
                 next = t;
@@ -246,7 +279,7 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
                 if (sp < kStack) {
                     stack[sp++] = t;
                 } else {
-                    P.link[t] = spill;
+                    wr_link(P, t, spill);
                     spill = t;
                 }
             }
@@ -262,7 +295,7 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
             }
             if (spill >= 0) {
                 cur = spill;
-                spill = P.link[cur];
+                spill = rd_link(P, cur);
                 continue;
             }
         }
@@ -274,12 +307,13 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
 // Arrival of n finished dependencies at cell u; starts a walker if complete.
 template <class E>
 __device__ __forceinline__ unsigned long long arrive(const Prob& P, int64_t u, uint32_t n) {
-    uint32_t got = counter_add(P.cnt, u, n);
+    uint32_t got = cnt_add(P, u, n);
     if (got == (uint32_t)__popc(g_deps<E>(P, u))) return run_walker<E>(P, u);
     return 0;
 }
 
 __device__ __forceinline__ uint32_t st_get(const uint32_t* st, int c) {
+    if (!FR_OK(c, kTileX * kTileY, 20)) return 0x0Fu;
     return (st[c >> 2] >> (8 * (c & 3))) & 0xFFu;
 }
 
@@ -295,11 +329,16 @@ __device__ __forceinline__ uint32_t intile_mask(int lx, int ly, int tw, int th) 
 }
 
 template <class E>
+__device__ __forceinline__ uint8_t s_rb(const Smem<E>& S, int i) {
+    return FR_OK(i, E::RX * E::RY, 21) ? S.rb[i] : E::kOobRb;
+}
+
+template <class E>
 __device__ __forceinline__ uint32_t s_donors(const Smem<E>& S, int lx, int ly) {
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        if ((recv_mask<E::kMfd>(S.rb[(ly + 1 + offy(k)) * E::RX + (lx + 1 + offx(k))]) >> opp(k)) & 1u)
+        if ((recv_mask<E::kMfd>(s_rb<E>(S, (ly + 1 + offy(k)) * E::RX + (lx + 1 + offx(k)))) >> opp(k)) & 1u)
             m |= 1u << k;
     return m;
 }
@@ -307,7 +346,7 @@ __device__ __forceinline__ uint32_t s_donors(const Smem<E>& S, int lx, int ly) {
 // Receivers of tile cell (lx, ly); gm is the cell's grid mask.
 template <class E>
 __device__ __forceinline__ uint32_t s_recv(const Smem<E>& S, int lx, int ly, uint32_t gm) {
-    return recv_mask<E::kMfd>(S.rb[(ly + 1) * E::RX + (lx + 1)]) & gm;
+    return recv_mask<E::kMfd>(s_rb<E>(S, (ly + 1) * E::RX + (lx + 1))) & gm;
 }
 
 template <class E>
@@ -332,7 +371,10 @@ __device__ __forceinline__ void q_push(Smem<E>& S, bool push, int t) {
     int base = 0;
     if (lane == (unsigned)(__ffs(b) - 1)) base = atomicAdd(&S.qtail, __popc(b));
     base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
-    if (push) S.q[base + __popc(b & ((1u << lane) - 1u))] = (uint16_t)t;
+    if (push) {
+        int slot = base + __popc(b & ((1u << lane) - 1u));
+        if (FR_OK(slot, E::NC, 22)) S.q[slot] = (uint16_t)t;
+    }
 }
 
 // Solves one tile: local phase, publication, cross-tile arrivals.
@@ -350,8 +392,8 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
         int ry = i / RX, rx = i - ry * RX;
         int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
         bool in = gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny;
-        S.rb[i] = in ? __ldg(P.rb + gy * P.nx + gx) : E::kOobRb;
-        if constexpr (E::kMfd) S.z[i] = in ? __ldg(P.z + gy * P.nx + gx) : __int_as_float(0x7f800000);
+        S.rb[i] = in ? rd_rb(P, gy * P.nx + gx) : E::kOobRb;
+        if constexpr (E::kMfd) S.z[i] = in ? rd_z(P, gy * P.nx + gx) : __int_as_float(0x7f800000);
     }
     if (tid == 0) S.qtail = 0;
     __syncthreads();
@@ -407,7 +449,7 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
             uint32_t tm = 0;
             bool glob = false;
             if (act) {
-                c = S.q[i];
+                c = FR_OK(i, NC, 23) ? S.q[i] : 0;
                 ly = c / TX;
                 lx = c - ly * TX;
                 glob = st_get(S.st, c) & kG;
@@ -427,6 +469,7 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
                         for (int k = 0; k < 8; ++k) {
                             if (!((dep >> k) & 1u)) continue;
                             int j = c + offy(k) * TX + offx(k);
+                            if (!FR_OK(j, NC, 24)) continue;
                             df vj = {S.vhi[j], S.vlo[j]};
                             if constexpr (E::kMfd) {
                                 float zj = S.z[(ly + 1 + offy(k)) * RX + lx + 1 + offx(k)];
@@ -444,7 +487,8 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
                         uint32_t a = S.area[c];
 #pragma unroll
                         for (int k = 0; k < 8; ++k)
-                            if ((dep >> k) & 1u) a += S.area[c + offy(k) * TX + offx(k)];
+                            if (((dep >> k) & 1u) && FR_OK(c + offy(k) * TX + offx(k), NC, 25))
+                                a += S.area[c + offy(k) * TX + offx(k)];
                         S.area[c] = a;
                     }
                     atomicOr(&S.st[c >> 2], kDone << (8 * (c & 3)));
@@ -454,7 +498,7 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
             for (int k = 0; k < 8; ++k) {
                 bool push = false;
                 int t = 0;
-                if ((tm >> k) & 1u) {
+                if (((tm >> k) & 1u) && FR_OK(c + offy(k) * TX + offx(k), NC, 26)) {
                     t = c + offy(k) * TX + offx(k);
                     uint32_t sh = 8u * (uint32_t)(t & 3);
                     if (glob) atomicOr(&S.st[t >> 2], kG << sh);
@@ -477,7 +521,7 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
         ++done;
         int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
         if constexpr (E::kVal) {
-            if (P.out_hi) P.out_hi[gi] = S.vhi[c];
+            if (P.out_hi) wr_f(P.out_hi, P, gi, S.vhi[c], 27);
             bool need_lo = P.lo_full;
             if (!need_lo) {
                 // a global cell or a cell of another tile will pull this value
@@ -489,9 +533,9 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
                     if (((tm & in) >> k) & 1u)
                         if (st_get(S.st, c + offy(k) * TX + offx(k)) & kG) need_lo = true;
             }
-            if (need_lo) P.out_lo[gi] = S.vlo[c];
+            if (need_lo) wr_f(P.out_lo, P, gi, S.vlo[c], 28);
         }
-        if constexpr (E::kArea) P.area[gi] = S.area[c];
+        if constexpr (E::kArea) wr_area(P, gi, S.area[c]);
     }
     __threadfence();
     __syncthreads();
@@ -516,7 +560,7 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
 #pragma unroll 1
             for (int k = 0; k < 8; ++k)
                 if ((tm >> k) & 1u)
-                    done += arrive<E>(P, gi + offy(k) * P.nx + offx(k), 1u);
+                    done += arrive<E>(P, gi + offi(k, P.nx), 1u);
         }
     }
     return done;

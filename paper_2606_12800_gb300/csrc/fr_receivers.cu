@@ -38,7 +38,8 @@ __device__ __forceinline__ void load_z_tile(float* zs, const float* __restrict__
         int ly = i / HX, lx = i - ly * HX;
         int64_t gx = x0 + lx - 2, gy = y0 + ly - 2;
         float v = inf;
-        if (gx >= 0 && gy >= 0 && gx < nx && gy < ny) v = __ldg(z + gy * nx + gx);
+        if (gx >= 0 && gy >= 0 && gx < nx && gy < ny && FR_OK(gy * nx + gx, nx * ny, 40))
+            v = __ldg(z + gy * nx + gx);
         zs[i] = v;
     }
 }
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ 
         int64_t gx = x0 + lx, gy = y0 + ly;
         if (gx >= nx || gy >= ny) continue;
         int64_t gi = gy * nx + gx;
+        if (!FR_OK(gi, nx * ny, 41)) continue;
         dir[gi] = ds[(ly + 1) * RX + lx + 1];
         if (INDEG) {
             int n = 0;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__
         int64_t gx = x0 + lx, gy = y0 + ly;
         if (gx >= nx || gy >= ny) continue;
         int64_t gi = gy * nx + gx;
+        if (!FR_OK(gi, nx * ny, 42)) continue;
         uint8_t m = ms[(ly + 1) * RX + lx + 1];
         mask[gi] = m;
         if (FRAC) {
@@ -224,3 +227,13 @@ cudaError_t launch_count_nonfinite(const float* z, int64_t n, unsigned long long
 }
 
 }  // namespace fr
+
+#ifdef FR_DEBUG_BOUNDS
+// Debug builds only: first out-of-range access seen by the receiver kernels.
+extern "C" unsigned long long fr_debug_bad_receivers(void) {
+    unsigned long long v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, fr::fr_debug_bad, sizeof(v));
+    cudaMemcpyToSymbol(fr::fr_debug_bad, &z, sizeof(z));
+    return v;
+}
+#endif

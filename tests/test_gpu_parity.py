@@ -110,7 +110,8 @@ def test_receivers_mfd(api, shape, flags):
     f = f.cpu().numpy().astype(np.float64)
     assert np.all((f == 0) == (f_ref == 0))
     nz = f_ref > 0
-    assert np.max(np.abs(f[nz] - f_ref[nz]) / f_ref[nz]) <= 2e-6
+    if nz.any():
+        assert np.max(np.abs(f[nz] - f_ref[nz]) / f_ref[nz]) <= 2e-6
 
 
 @pytest.mark.parametrize("shape", [(1, 9), (33, 65), (97, 131), (256, 256), (300, 517)])
