@@ -303,7 +303,7 @@ def main():
                      "traffic": None, "algorithmic_bytes_per_cell": 17,
                      "step_frac": step_bytes / (total_ms / K * 1e-3) / 1e9 / peak},
         "e2e": e2e,
-        "gpu_launches": K * 4,
+        "gpu_launches": K * 5,
         "clocks": clk,
     }
     if cpu:

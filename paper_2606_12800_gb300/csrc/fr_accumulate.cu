@@ -8,12 +8,15 @@ namespace {
 template <Mode M, bool W, bool A>
 cudaError_t launch_single(const Prob& P, EngineGlobals* G, cudaStream_t s) {
     constexpr size_t sm = engine_smem<M, W, A>();
-    cudaError_t e = cudaFuncSetAttribute(k_engine<M, W, A>,
+    cudaError_t e = cudaFuncSetAttribute(k_local<M, W, A>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int64_t tiles_y = (P.ny + kTileY - 1) / kTileY;
     const int64_t tiles = tiles_y * P.tiles_x;
-    k_engine<M, W, A><<<(unsigned)tiles, 256, sm, s>>>(P, G);
+    k_local<M, W, A><<<(unsigned)tiles, 256, sm, s>>>(P, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_global<M, W, A><<<walker_grid(), 256, 0, s>>>(nullptr, P, G, (unsigned long long)(P.nx * P.ny));
     return cudaGetLastError();
 }
 
@@ -22,10 +25,14 @@ cudaError_t launch_batch(const Prob* probs, const int64_t* prefix, int nprob, in
                          unsigned long long total_cells, EngineGlobals* G, int grid,
                          cudaStream_t s) {
     constexpr size_t sm = engine_smem<M, W, A>();
-    cudaError_t e = cudaFuncSetAttribute(k_engine_batch<M, W, A>,
+    cudaError_t e = cudaFuncSetAttribute(k_local_batch<M, W, A>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_engine_batch<M, W, A><<<grid, 256, sm, s>>>(probs, prefix, nprob, total_tiles, total_cells, G);
+    k_local_batch<M, W, A><<<grid, 256, sm, s>>>(probs, prefix, nprob, total_tiles, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Prob none{};
+    k_global<M, W, A><<<walker_grid(), 256, 0, s>>>(probs, none, G, total_cells);
     return cudaGetLastError();
 }
 
@@ -218,6 +225,18 @@ __global__ void __launch_bounds__(GNT) k_mfd_grad_z(Prob P, const float* __restr
 }
 
 }  // namespace
+
+// Persistent walker grid: a few CTAs per SM, grid-striding over the list.
+int walker_grid() {
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = (sms > 0 ? sms : 152) * 8;
+    }
+    return grid;
+}
 
 cudaError_t launch_engine(Mode mode, bool want_w, bool want_area, const Prob& P,
                           EngineGlobals* G, cudaStream_t s) {

@@ -17,11 +17,12 @@ constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Workspace layout (same for every operation on an nx*ny grid):
-//   globals (64 B) | arrival counters (1 B/cell) | trailing words (4 B/cell)
-//   | walker links (8 B/cell) | routing bytes (1 B/cell) | mass partials
-// The first two regions are zeroed by each engine call (one memset).
+//   globals (64 B) | arrival counters (1 B/cell) | global-cell bits (1 bit/cell)
+//   | trailing words (4 B/cell) | walker links (8 B/cell)
+//   | global-cell list (8 B/cell) | routing bytes (1 B/cell) | mass partials
+// The first three regions are zeroed by each engine call (one memset).
 struct Layout {
-    size_t cnt, lo, link, rb, partials, total, zero_bytes;
+    size_t cnt, gbits, lo, link, glist, rb, partials, total, zero_bytes;
 };
 
 Layout layout(int64_t n) {
@@ -29,10 +30,14 @@ Layout layout(int64_t n) {
     size_t off = 256;
     L.cnt = off;
     off += align256((size_t)n + 4);
+    L.gbits = off;
+    off += align256(((size_t)n + 31) / 32 * 4);
     L.zero_bytes = off;
     L.lo = off;
     off += align256((size_t)n * 4);
     L.link = off;
+    off += align256((size_t)n * 8);
+    L.glist = off;
     off += align256((size_t)n * 8);
     L.rb = off;
     off += align256((size_t)n);
@@ -91,6 +96,9 @@ Prob base_prob(const fr_routing* R, char* ws) {
     P.z = R->kind == FR_ROUTING_MFD ? R->dem : nullptr;
     P.cnt = reinterpret_cast<uint32_t*>(ws + L.cnt);
     P.link = reinterpret_cast<int64_t*>(ws + L.link);
+    P.gbits = reinterpret_cast<uint32_t*>(ws + L.gbits);
+    P.glist = reinterpret_cast<unsigned long long*>(ws + L.glist);
+    P.glist_cap = R->nx * R->ny;
     P.out_lo = reinterpret_cast<float*>(ws + L.lo);
     P.mc = make_mfd_const(R->kind == FR_ROUTING_MFD ? R->dx : 1.0, R->kind == FR_ROUTING_MFD ? R->p : 1.0);
     P.tiles_x = (int32_t)((R->nx + kTileX - 1) / kTileX);
@@ -191,9 +199,10 @@ fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, fl
     const Layout L = layout(n);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, s);
     if (e != cudaSuccess) return FR_ERR_CUDA;
-    const Mode m = R->kind == FR_ROUTING_D8 ? Mode::FwdD8 : Mode::FwdMfd;
-    return cuda_status(launch_engine(m, w_out != nullptr, area_out != nullptr, P,
-                                     reinterpret_cast<EngineGlobals*>(ws), s));
+    EngineGlobals* G = reinterpret_cast<EngineGlobals*>(ws);
+    if (R->kind == FR_ROUTING_D8)
+        return cuda_status(launch_d8_forward(w_out != nullptr, area_out != nullptr, P, G, s));
+    return cuda_status(launch_engine(Mode::FwdMfd, true, false, P, G, s));
 }
 
 fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,

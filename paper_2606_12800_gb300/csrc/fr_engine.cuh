@@ -14,14 +14,15 @@
 //     shared-memory queue appended with warp-aggregated atomics.  Cells with a
 //     dependency outside the tile (and everything they feed inside it) are
 //     marked "global".
-//  2. global phase: instead of the paper's Richardson iteration across
-//     subdomain boundaries (App. B.1), cross-tile dependencies are resolved
-//     exactly and without waiting: every cell has an arrival counter, each
-//     finished dependency increments it, and the thread that brings it to the
-//     cell's dependency count computes the cell ("last arriver continues") and
-//     walks on downstream.  Work is O(N) and no thread ever waits on another,
-//     so a routing graph with a cycle cannot hang the kernel: its cells are
-//     simply never reached, which the completion count reports.
+//  2. global phase (a second kernel, after every tile is done): instead of
+//     the paper's Richardson iteration across subdomain boundaries (App. B.1),
+//     the global cells are solved exactly and without waiting.  Each global
+//     cell has an arrival counter for its global dependencies; a global cell
+//     with none starts a walker, each finished cell increments its targets'
+//     counters, and the thread that completes a counter computes that cell
+//     ("last arriver continues").  Work is O(N), no thread ever waits on
+//     another, and a routing graph with a cycle cannot hang the kernel: its
+//     cells are never reached, which the completion count reports.
 //
 // Values are pulled from dependencies in a fixed neighbour order, so results
 // are bit-reproducible.  Real-valued sums are two-float (fp32 hi + lo); unit
@@ -39,6 +40,7 @@ struct Eng {
     static constexpr bool kVal = W || kAdj || kMfd;      // two-float values are solved
     static constexpr bool kArea = AREA && (M == Mode::FwdD8);
     static constexpr bool kBranch = kMfd || kAdj;         // several targets per cell
+    static constexpr bool kD8Fwd = (M == Mode::FwdD8);
     static constexpr int TX = kTileX, TY = kTileY, NC = TX * TY;
     static constexpr int RX = TX + 2, RY = TY + 2;
     static constexpr int NT = 256;
@@ -58,7 +60,8 @@ struct alignas(16) Smem {
     float z[E::kMfd ? E::RX * E::RY : 1];
     uint32_t area[E::kArea ? E::NC : 1];
     uint32_t st[E::NC / 4];
-    uint16_t q[E::NC];
+    uint16_t q[E::kD8Fwd ? 1 : E::NC];
+    uint8_t dm[E::kD8Fwd ? E::NC : 1];
     uint8_t rb[E::RX * E::RY];
     int qtail;
     int64_t work;
@@ -248,11 +251,28 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
 constexpr int kStack = 8;
 constexpr unsigned kStatusNoProgress = 5u;
 
-// Walks downstream (forward) or upstream (adjoint) from a ready cell.  Cells
-// that become ready along the way are continued by this thread: one directly,
-// further ones on a small private stack that spills into a linked list threaded
-// through P.link (each cell becomes ready exactly once, so every cell owns its
-// link slot and nothing needs clearing).  Returns the number of cells computed.
+__device__ __forceinline__ bool gbit(const Prob& P, int64_t i) {
+    return FR_OK(i, ncell(P), 15) ? ((__ldg(P.gbits + (i >> 5)) >> (i & 31)) & 1u) : false;
+}
+
+// Number of dependencies of cell i that are global (solved by walkers).
+template <class E>
+__device__ __forceinline__ uint32_t g_deps_global(const Prob& P, int64_t i) {
+    const uint32_t dep = g_deps<E>(P, i);
+    uint32_t n = 0;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k)
+        if ((dep >> k) & 1u) n += gbit(P, i + offi(k, P.nx));
+    return n;
+}
+
+// Walks downstream (forward) or upstream (adjoint) from a ready global cell.
+// Cells that become ready along the way are continued by this thread: one
+// directly, further ones on a small private stack that spills into a linked
+// list threaded through P.link (each cell becomes ready exactly once, so every
+// cell owns its link slot and nothing needs clearing).  Targets that are not
+// global were solved exactly by their own tile and are skipped.  Returns the
+// number of cells computed.
 template <class E>
 __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t start) {
     unsigned long long n = 0;
@@ -266,13 +286,14 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
         __threadfence();
         const uint32_t tm = g_targets<E>(P, cur);
         int64_t next = -1;
-        const int64_t y = cur / P.nx, x = cur - y * P.nx;
 #pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             if (!((tm >> k) & 1u)) continue;
             int64_t t = cur + offi(k, P.nx);
+            // with overlapping tile regions a target may already be final
+            if (!gbit(P, t)) continue;
             uint32_t got = cnt_add(P, t, 1u);
-            if (got != (uint32_t)__popc(g_deps<E>(P, t))) continue;
+            if (got != g_deps_global<E>(P, t)) continue;
             if (next < 0) {
                 next = t;
             } else if constexpr (E::kBranch) {
@@ -285,15 +306,18 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
             }
         }
         if (next >= 0) {
+            __threadfence();
             cur = next;
             continue;
         }
         if constexpr (E::kBranch) {
             if (sp > 0) {
+                __threadfence();
                 cur = stack[--sp];
                 continue;
             }
             if (spill >= 0) {
+                __threadfence();
                 cur = spill;
                 spill = rd_link(P, cur);
                 continue;
@@ -304,14 +328,6 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
     return n;
 }
 
-// Arrival of n finished dependencies at cell u; starts a walker if complete.
-template <class E>
-__device__ __forceinline__ unsigned long long arrive(const Prob& P, int64_t u, uint32_t n) {
-    uint32_t got = cnt_add(P, u, n);
-    if (got == (uint32_t)__popc(g_deps<E>(P, u))) return run_walker<E>(P, u);
-    return 0;
-}
-
 __device__ __forceinline__ uint32_t st_get(const uint32_t* st, int c) {
     if (!FR_OK(c, kTileX * kTileY, 20)) return 0x0Fu;
     return (st[c >> 2] >> (8 * (c & 3))) & 0xFFu;
@@ -319,6 +335,7 @@ __device__ __forceinline__ uint32_t st_get(const uint32_t* st, int c) {
 
 // In-tile neighbour mask of tile cell (lx, ly) in a tile of tw x th cells.
 __device__ __forceinline__ uint32_t intile_mask(int lx, int ly, int tw, int th) {
+    if (lx > 0 && ly > 0 && lx < tw - 1 && ly < th - 1) return 0xFFu;
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -377,9 +394,34 @@ __device__ __forceinline__ void q_push(Smem<E>& S, bool push, int t) {
     }
 }
 
-// Solves one tile: local phase, publication, cross-tile arrivals.
+// Marks a global cell: sets its bit and appends it to the global list.  All
+// 32 lanes call it together; lanes of a warp hold consecutive cells of a tile
+// row, so the bit updates are merged per 32-bit word.
+__device__ __forceinline__ void mark_global(const Prob& P, EngineGlobals* G, bool glob,
+                                            int64_t gi, int pid) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned b = __ballot_sync(0xffffffffu, glob);
+    if (!b) return;
+    const unsigned long long word = glob ? (unsigned long long)(gi >> 5) : ~0ull - lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, word);
+    const unsigned acc = __reduce_or_sync(peers, glob ? (1u << (gi & 31)) : 0u);
+    if (glob && lane == (unsigned)(__ffs(peers) - 1) && FR_OK(gi, ncell(P), 16))
+        atomicOr(P.gbits + (gi >> 5), acc);
+    unsigned long long base = 0;
+    if (lane == (unsigned)(__ffs(b) - 1))
+        base = atomicAdd(&G->glist_count, (unsigned long long)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+    if (glob) {
+        const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
+        if (FR_OK((int64_t)slot, P.glist_cap, 17))
+            P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
+    }
+}
+
+// Local phase of one tile (generic modes): level-synchronous wavefront.
 template <class E>
-__device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty, Smem<E>& S) {
+__device__ unsigned long long process_tile(const Prob& P, int pid, int64_t tx, int64_t ty,
+                                           Smem<E>& S, EngineGlobals* G) {
     constexpr int TX = E::TX, NC = E::NC, RX = E::RX, RY = E::RY, NT = E::NT;
     const int tid = threadIdx.x;
     const int64_t x0 = tx * TX, y0 = ty * E::TY;
@@ -512,14 +554,15 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
         begin = end;
     }
 
-    // publish locally solved cells (row-major, coalesced)
+    // publish locally solved cells (row-major, coalesced); list global cells
     for (int c = tid; c < NC; c += NT) {
         int ly = c / TX, lx = c - ly * TX;
-        if (lx >= tw || ly >= th) continue;
-        uint32_t b = st_get(S.st, c);
-        if (!(b & kDone)) continue;
+        const bool valid = lx < tw && ly < th;
+        const uint32_t b = valid ? st_get(S.st, c) : 0u;
+        const int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
+        mark_global(P, G, valid && (b & kG), gi, pid);
+        if (!valid || !(b & kDone)) continue;
         ++done;
-        int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
         if constexpr (E::kVal) {
             if (P.out_hi) wr_f(P.out_hi, P, gi, S.vhi[c], 27);
             bool need_lo = P.lo_full;
@@ -537,76 +580,174 @@ __device__ unsigned long long process_tile(const Prob& P, int64_t tx, int64_t ty
         }
         if constexpr (E::kArea) wr_area(P, gi, S.area[c]);
     }
-    __threadfence();
+    return done;
+}
+
+// --------------------------------------------------------- D8 forward tile
+// Specialised local phase for D8 forward routing: every tile cell has at most
+// one receiver, so a finished cell is continued by the thread that completes
+// its receiver's count ("last arriver", shared-memory atomics), with no
+// rounds and no barriers inside the solve.
+template <class E>
+__device__ unsigned long long process_tile_d8(const Prob& P, int pid, int64_t tx, int64_t ty,
+                                              Smem<E>& S, EngineGlobals* G) {
+    constexpr int TX = E::TX, NC = E::NC, RX = E::RX, RY = E::RY, NT = E::NT;
+    const int tid = threadIdx.x;
+    const int64_t x0 = tx * TX, y0 = ty * E::TY;
+    const int tw = (int)(P.nx - x0 < TX ? P.nx - x0 : TX);
+    const int th = (int)(P.ny - y0 < E::TY ? P.ny - y0 : E::TY);
+    unsigned long long done = 0;
+
+    for (int i = tid; i < RX * RY; i += NT) {
+        int ry = i / RX, rx = i - ry * RX;
+        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
+        bool in = gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny;
+        uint8_t code = in ? rd_rb(P, gy * P.nx + gx) : kSink;
+        if (code < 8) {  // receivers outside the grid act as none
+            int64_t xr = gx + offx(code), yr = gy + offy(code);
+            if (xr < 0 || yr < 0 || xr >= P.nx || yr >= P.ny) code = kSink;
+        } else {
+            code = kSink;
+        }
+        S.rb[i] = code;
+    }
     __syncthreads();
 
-    // arrivals at global cells of this tile and at cells of neighbouring tiles
+    uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
     for (int c = tid; c < NC; c += NT) {
         int ly = c / TX, lx = c - ly * TX;
-        if (lx >= tw || ly >= th) continue;
-        uint32_t b = st_get(S.st, c);
-        int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
-        uint32_t in = intile_mask(lx, ly, tw, th);
-        const uint32_t gm = grid_mask(x0 + lx, y0 + ly, P.nx, P.ny);
-        if (b & kG) {
-            uint32_t dep = s_deps<E>(S, lx, ly, gm) & in;
-            uint32_t n = 0;
+        uint8_t b = 0x0F;
+        if (lx < tw && ly < th) {
+            const int r = (ly + 1) * RX + lx + 1;
+            uint32_t dm = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                if ((dep >> k) & 1u) n += !(st_get(S.st, c + offy(k) * TX + offx(k)) & kG);
-            if (n) done += arrive<E>(P, gi, n);
-        } else if (b & kDone) {
-            uint32_t tm = s_targets<E>(S, lx, ly, gm) & ~in;
-#pragma unroll 1
-            for (int k = 0; k < 8; ++k)
-                if ((tm >> k) & 1u)
-                    done += arrive<E>(P, gi + offi(k, P.nx), 1u);
+                dm |= (uint32_t)(S.rb[r + offy(k) * RX + offx(k)] == (uint8_t)opp(k)) << k;
+            const uint32_t in = intile_mask(lx, ly, tw, th);
+            b = (uint8_t)(__popc(dm & in) | ((dm & ~in) ? kG : 0u));
+            S.dm[c] = (uint8_t)(dm & in);
+            const int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
+            if constexpr (E::kVal) {
+                S.vhi[c] = P.init ? rd_in(P.init, P, gi, 8) : 1.0f;
+                S.vlo[c] = 0.0f;
+            }
+            if constexpr (E::kArea) S.area[c] = 1u;
         }
+        stb[c] = b;
+    }
+    __syncthreads();
+
+    // chain walks from the cells whose in-tile donors are all... none
+    for (int c0 = tid; c0 < NC; c0 += NT) {
+        {
+            int ly = c0 / TX, lx = c0 - ly * TX;
+            if (lx >= tw || ly >= th || S.dm[c0] != 0) continue;
+        }
+        int c = c0;
+        while (true) {
+            const int ly = c / TX, lx = c - ly * TX;
+            const uint32_t b = st_get(S.st, c);
+            const bool glob = b & kG;
+            if (!glob) {
+                const uint32_t dm = S.dm[c];
+                if constexpr (E::kVal) {
+                    df v = {S.vhi[c], S.vlo[c]};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if ((dm >> k) & 1u) {
+                            const int j = c + offy(k) * TX + offx(k);
+                            v = df_add(v, df{S.vhi[j], S.vlo[j]});
+                        }
+                    S.vhi[c] = v.hi;
+                    S.vlo[c] = v.lo;
+                }
+                if constexpr (E::kArea) {
+                    uint32_t a = S.area[c];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if ((dm >> k) & 1u) a += S.area[c + offy(k) * TX + offx(k)];
+                    S.area[c] = a;
+                }
+            }
+            const uint8_t code = S.rb[(ly + 1) * RX + lx + 1];
+            atomicOr(&S.st[c >> 2], kDone << (8 * (c & 3)));
+            if (code >= 8) break;
+            const int xr = lx + offx(code), yr = ly + offy(code);
+            if (xr < 0 || yr < 0 || xr >= tw || yr >= th) break;  // leaves the tile
+            const int t = yr * TX + xr;
+            const uint32_t sh = 8u * (uint32_t)(t & 3);
+            if (glob) atomicOr(&S.st[t >> 2], kG << sh);
+            __threadfence_block();
+            const uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
+            if (((old >> sh) & 0x0Fu) != 1u) break;
+            __threadfence_block();
+            c = t;
+        }
+    }
+    __syncthreads();
+
+    for (int c = tid; c < NC; c += NT) {
+        int ly = c / TX, lx = c - ly * TX;
+        const bool valid = lx < tw && ly < th;
+        const uint32_t b = valid ? st_get(S.st, c) : 0u;
+        const int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
+        mark_global(P, G, valid && (b & kG), gi, pid);
+        if (!valid || (b & kG) || !(b & kDone)) continue;
+        ++done;
+        if constexpr (E::kVal) {
+            wr_f(P.out_hi, P, gi, S.vhi[c], 27);
+            bool need_lo = P.lo_full;
+            if (!need_lo) {
+                const uint8_t code = S.rb[(ly + 1) * RX + lx + 1];
+                if (code < 8) {
+                    const int xr = lx + offx(code), yr = ly + offy(code);
+                    need_lo = (xr < 0 || yr < 0 || xr >= tw || yr >= th) ||
+                              (st_get(S.st, yr * TX + xr) & kG);
+                }
+            }
+            if (need_lo) wr_f(P.out_lo, P, gi, S.vlo[c], 28);
+        }
+        if constexpr (E::kArea) wr_area(P, gi, S.area[c]);
     }
     return done;
 }
 
-// Block-wide sum of per-thread done counts, added once per CTA; the last CTA
-// to finish compares the total with the expected cell count.
 template <class E>
-__device__ void finish_cta(Smem<E>& S, unsigned long long done, EngineGlobals* G,
-                           unsigned long long total_cells) {
+__device__ __forceinline__ unsigned long long solve_tile(const Prob& P, int pid, int64_t tx,
+                                                         int64_t ty, Smem<E>& S, EngineGlobals* G) {
+    if constexpr (E::kD8Fwd) return process_tile_d8<E>(P, pid, tx, ty, S, G);
+    else return process_tile<E>(P, pid, tx, ty, S, G);
+}
+
+// Block-wide sum of per-thread counts, added once per CTA.
+template <class E>
+__device__ void add_done(Smem<E>& S, unsigned long long done, EngineGlobals* G) {
     for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
     if (threadIdx.x == 0) S.done = 0;
     __syncthreads();
     if ((threadIdx.x & 31) == 0 && done) atomicAdd(&S.done, done);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (S.done) atomicAdd(&G->done_cells, S.done);
-        __threadfence();
-        unsigned fin = atomicAdd(&G->finished_ctas, 1u);
-        if (fin == gridDim.x - 1) {
-            __threadfence();
-            unsigned long long got = atomicAdd(&G->done_cells, 0ull);
-            if (got != total_cells) atomicMax(&G->status, kStatusNoProgress);
-        }
-    }
+    if (threadIdx.x == 0 && S.done) atomicAdd(&G->done_cells, S.done);
 }
 
+// Local phase over all tiles of one problem (one CTA per tile).
 template <Mode M, bool W, bool AREA>
-__global__ void __launch_bounds__(256) k_engine(Prob P, EngineGlobals* G) {
+__global__ void __launch_bounds__(256) k_local(Prob P, EngineGlobals* G) {
     using E = Eng<M, W, AREA>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<E>& S = *reinterpret_cast<Smem<E>*>(smem_raw);
     const int64_t tile = blockIdx.x;
     const int64_t ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
-    unsigned long long done = process_tile<E>(P, tx, ty, S);
-    finish_cta<E>(S, done, G, (unsigned long long)(P.nx * P.ny));
+    add_done<E>(S, solve_tile<E>(P, 0, tx, ty, S, G), G);
 }
 
-// Persistent batched form: CTAs claim tiles of any problem from a global
-// counter until all are taken.  tile_prefix[p] is the first tile of problem p.
+// Local phase, batched: CTAs claim tiles of any problem from a global counter.
+// tile_prefix[p] is the first tile of problem p.
 template <Mode M, bool W, bool AREA>
-__global__ void __launch_bounds__(256) k_engine_batch(const Prob* __restrict__ probs,
-                                                      const int64_t* __restrict__ tile_prefix,
-                                                      int nprob, int64_t total_tiles,
-                                                      unsigned long long total_cells,
-                                                      EngineGlobals* G) {
+__global__ void __launch_bounds__(256) k_local_batch(const Prob* __restrict__ probs,
+                                                     const int64_t* __restrict__ tile_prefix,
+                                                     int nprob, int64_t total_tiles,
+                                                     EngineGlobals* G) {
     using E = Eng<M, W, AREA>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<E>& S = *reinterpret_cast<Smem<E>*>(smem_raw);
@@ -626,10 +767,46 @@ __global__ void __launch_bounds__(256) k_engine_batch(const Prob* __restrict__ p
         const Prob P = probs[lo];
         const int64_t lt = w - tile_prefix[lo];
         const int64_t ty = lt / P.tiles_x, tx = lt - ty * P.tiles_x;
-        done += process_tile<E>(P, tx, ty, S);
+        done += solve_tile<E>(P, lo, tx, ty, S, G);
         __syncthreads();
     }
-    finish_cta<E>(S, done, G, total_cells);
+    add_done<E>(S, done, G);
+}
+
+// Global phase: grid-stride over the global-cell list; cells with no global
+// dependency start walkers.  The last CTA to finish checks that every cell of
+// every problem was computed.
+template <Mode M, bool W, bool AREA>
+__global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, Prob single,
+                                                EngineGlobals* G, unsigned long long total_cells) {
+    using E = Eng<M, W, AREA>;
+    __shared__ unsigned long long s_done;
+    const unsigned long long count = G->glist_count;
+    const unsigned long long* list = probs ? probs[0].glist : single.glist;
+    unsigned long long done = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long item = __ldcg(list + i);
+        const int pid = (int)(item >> 40);
+        const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
+        const Prob& P = probs ? probs[pid] : single;
+        if (g_deps_global<E>(P, cell) == 0) done += run_walker<E>(P, cell);
+    }
+    for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
+    if (threadIdx.x == 0) s_done = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && done) atomicAdd(&s_done, done);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_done) atomicAdd(&G->done_cells, s_done);
+        __threadfence();
+        unsigned fin = atomicAdd(&G->finished_ctas, 1u);
+        if (fin == gridDim.x - 1) {
+            __threadfence();
+            unsigned long long got = atomicAdd(&G->done_cells, 0ull);
+            if (got != total_cells) atomicMax(&G->status, kStatusNoProgress);
+        }
+    }
 }
 
 template <Mode M, bool W, bool AREA>

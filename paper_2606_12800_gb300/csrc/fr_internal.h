@@ -34,6 +34,9 @@ struct Prob {
     uint64_t* area;        // D8 forward unit-rain areas or NULL
     uint32_t* cnt;         // packed byte arrival counters, zeroed before the launch
     int64_t* link;         // per-cell spill links of the walkers (no init needed)
+    uint32_t* gbits;       // one bit per cell: "global" (solved by the walkers), zeroed
+    unsigned long long* glist;  // compact list of global cells (pid << 40 | cell)
+    int64_t glist_cap;     // capacity of glist (entries)
     MfdConst mc;
     int32_t lo_full;       // out_lo is a user output: write it for every cell
     int32_t tiles_x;       // number of CTA tiles along x
@@ -46,21 +49,27 @@ struct EngineGlobals {
     unsigned long long done_cells;   // cells whose value was computed
     unsigned long long work_next;    // batched: next tile to claim
     unsigned long long nonfinite;    // FR_CHECK_FINITE: count of NaN/Inf inputs
-    unsigned int finished_ctas;      // CTAs that have left the kernel
+    unsigned int finished_ctas;      // walker CTAs that have left the kernel
     unsigned int status;             // fr_status of the device-side checks
-    unsigned long long pad[4];
+    unsigned long long glist_count;  // entries in the global-cell list
+    unsigned long long pad[3];
 };
 static_assert(sizeof(EngineGlobals) == 64, "globals block is 64 bytes");
 
 enum class Mode : int { FwdD8 = 0, FwdMfd = 1, AdjD8 = 2, AdjMfd = 3 };
 
-// Tile engine launches (fr_accumulate.cu).
+// Tile engine launches (fr_accumulate.cu): the tile kernel (local phase) and
+// the walker kernel (global phase), in stream order.
 cudaError_t launch_engine(Mode mode, bool want_w, bool want_area, const Prob& prob,
                           EngineGlobals* g, cudaStream_t s);
 cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Prob* probs_dev,
                                 const int64_t* tile_prefix_dev, int32_t nprob,
                                 int64_t total_tiles, unsigned long long total_cells,
                                 EngineGlobals* g, int grid, cudaStream_t s);
+int walker_grid();
+// D8 forward: halo-tile local phase (fr_d8.cu) + walker phase.
+cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
+                              cudaStream_t s);
 cudaError_t launch_mfd_grad_z(const Prob& prob, const float* g_hi, const float* g_lo,
                               float* dLdz, cudaStream_t s);
 cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t* rb,

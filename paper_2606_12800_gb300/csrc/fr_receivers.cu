@@ -26,7 +26,7 @@ MfdConst make_mfd_const(double dx, double p) {
 namespace {
 
 constexpr int RTX = 128;  // receiver tile width (cells)
-constexpr int RTY = 8;    // receiver tile height
+constexpr int RTY = 16;   // receiver tile height
 constexpr int RNT = 256;  // threads
 constexpr int HX = RTX + 4, HY = RTY + 4;
 constexpr int RX = RTX + 2, RY = RTY + 2;
@@ -58,6 +58,9 @@ __device__ __forceinline__ void tile_origin(int64_t nx, int64_t& x0, int64_t& y0
     y0 = ty * RTY;
 }
 
+// D8 codes of RTX x RTY tile cells; each thread computes four consecutive
+// cells of a row from a 3 x 6 register window.  Tiles away from the grid
+// boundary skip all edge and bounds tests.
 template <bool INDEG>
 __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ z, int64_t nx,
                                                       int64_t ny, float c_orth, float c_diag,
@@ -67,39 +70,80 @@ __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ 
     __shared__ uint8_t ds[RX * RY];
     int64_t x0, y0;
     tile_origin(nx, x0, y0);
-    load_z_tile(zs, z, nx, ny, x0, y0);
-    __syncthreads();
     const bool lowest = flags & kD8Lowest;
     const bool edge_route = flags & kEdgeRoute;
-    // routing byte for the tile (+ ring when donor counts are wanted)
-    const int rx0 = INDEG ? 0 : 1, ry0 = INDEG ? 0 : 1;
-    const int rw = INDEG ? RX : RTX, rh = INDEG ? RY : RTY;
-    for (int i = threadIdx.x; i < rw * rh; i += RNT) {
-        int ry = ry0 + i / rw, rx = rx0 + i % rw;
-        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
-        uint8_t code = kSink;
-        if (gx >= 0 && gy >= 0 && gx < nx && gy < ny &&
-            (edge_route || !is_edge(gx, gy, nx, ny))) {
-            float zn[8];
-            gather8(zs, rx, ry, zn);
-            code = d8_code(zs[(ry + 1) * HX + (rx + 1)], zn, c_orth, c_diag, lowest);
+    const bool interior = x0 >= 2 && y0 >= 2 && x0 + RTX + 2 <= nx && y0 + RTY + 2 <= ny;
+    if (interior) {
+        const float* base = z + (y0 - 2) * nx + (x0 - 2);
+        for (int i = threadIdx.x; i < HX * HY; i += RNT) {
+            const int ly = i / HX, lx = i - ly * HX;
+            zs[i] = __ldg(base + (int64_t)ly * nx + lx);
         }
-        ds[ry * RX + rx] = code;
+    } else {
+        load_z_tile(zs, z, nx, ny, x0, y0);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < RTX * RTY; i += RNT) {
-        int ly = i / RTX, lx = i - ly * RTX;
-        int64_t gx = x0 + lx, gy = y0 + ly;
-        if (gx >= nx || gy >= ny) continue;
-        int64_t gi = gy * nx + gx;
-        if (!FR_OK(gi, nx * ny, 41)) continue;
-        dir[gi] = ds[(ly + 1) * RX + lx + 1];
-        if (INDEG) {
+    // four cells per thread: tile row r = (t >> 5) + 8 j, columns 4 (t & 31) .. + 3
+    const int qx = (threadIdx.x & 31) * 4;
+    for (int r = threadIdx.x >> 5; r < RTY; r += RNT / 32) {
+        float w[3][6];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 6; ++b) w[a][b] = zs[(r + 1 + a) * HX + qx + 1 + b];
+        uint32_t packed = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float zn[8] = {w[1][q + 2], w[0][q + 1], w[1][q], w[2][q + 1],
+                                 w[0][q + 2], w[0][q], w[2][q], w[2][q + 2]};
+            uint8_t code = d8_code(w[1][q + 1], zn, c_orth, c_diag, lowest);
+            if (!interior) {  // interior tiles hold no edge cell and no cell off the grid
+                const int64_t gx = x0 + qx + q, gy = y0 + r;
+                if (gx >= nx || gy >= ny || (!edge_route && is_edge(gx, gy, nx, ny))) code = kSink;
+            }
+            packed |= (uint32_t)code << (8 * q);
+            if (INDEG) ds[(r + 1) * RX + qx + q + 1] = code;
+        }
+        const int64_t gy = y0 + r;
+        if (gy < ny) {
+            const int64_t gi = gy * nx + x0 + qx;
+            if (interior && ((uintptr_t)(dir + gi) & 3) == 0) {
+                *reinterpret_cast<uint32_t*>(dir + gi) = packed;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (x0 + qx + q < nx) dir[gi + q] = (uint8_t)(packed >> (8 * q));
+            }
+        }
+    }
+    if (INDEG) {
+        // the ring around the tile, then the donor counts
+        for (int i = threadIdx.x; i < 2 * RX + 2 * RTY; i += RNT) {
+            int ry, rx;
+            if (i < RX) { ry = 0; rx = i; }
+            else if (i < 2 * RX) { ry = RY - 1; rx = i - RX; }
+            else if (i < 2 * RX + RTY) { ry = i - 2 * RX + 1; rx = 0; }
+            else { ry = i - 2 * RX - RTY + 1; rx = RX - 1; }
+            const int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
+            uint8_t code = kSink;
+            if (gx >= 0 && gy >= 0 && gx < nx && gy < ny &&
+                (edge_route || !is_edge(gx, gy, nx, ny))) {
+                float zn[8];
+                gather8(zs, rx, ry, zn);
+                code = d8_code(zs[(ry + 1) * HX + (rx + 1)], zn, c_orth, c_diag, lowest);
+            }
+            ds[ry * RX + rx] = code;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < RTX * RTY; i += RNT) {
+            const int ly = i / RTX, lx = i - ly * RTX;
+            const int64_t gx = x0 + lx, gy = y0 + ly;
+            if (gx >= nx || gy >= ny) continue;
             int n = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 n += ds[(ly + 1 + offy(k)) * RX + (lx + 1 + offx(k))] == (uint8_t)opp(k);
-            indeg[gi] = (uint8_t)n;
+            indeg[gy * nx + gx] = (uint8_t)n;
         }
     }
 }

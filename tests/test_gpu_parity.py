@@ -218,3 +218,32 @@ def test_routing_pointing_outside_grid_is_a_sink(api):
     a = out["area"].cpu().numpy()
     assert a[5, 6] == 2 and a.sum() == ny * nx + 1
     assert api.get_status() == 0
+
+
+@pytest.mark.parametrize("shape,seed", [((2048, 1536), 3), ((1500, 2600), 7)])
+def test_route_d8_large(api, shape, seed):
+    """Many tiles: cross-tile chains, halo overlaps and walkers all occur."""
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, seed=seed)
+    rain = inputs.rain_field(ny, nx, seed)
+    out = api.route_d8(cuda(z), 30.0, cuda(rain), 0, want_w=True, want_lo=True, want_area=True)
+    assert api.get_status() == 0
+    d_ref, w_ref, _, order = oracle.route_d8(z, 30.0, rain)
+    _, a_ref = oracle.accumulate_d8(d_ref, order, None)
+    np.testing.assert_array_equal(out["area"].cpu().numpy().astype(np.uint64), a_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+def test_d8_benchmark_workload_full_size(api):
+    """The 4096^2 benchmark workload (beta 2, tilt 0.01, rain U[0,1)): areas
+    bit-exact and water within 1e-6 of the full FP64 oracle."""
+    n = 4096
+    z = inputs.fractal_dem(n, n, beta=2.0, tilt=0.01, seed=1)
+    rain = inputs.rain_field(n, n, 1)
+    out = api.route_d8(cuda(z), 30.0, cuda(rain), 0, want_w=True, want_area=True, want_dir=True)
+    assert api.get_status() == 0
+    d_ref, w_ref, _, order = oracle.route_d8(z, 30.0, rain)
+    np.testing.assert_array_equal(out["dir"].cpu().numpy(), d_ref)
+    _, a_ref = oracle.accumulate_d8(d_ref, order, None)
+    np.testing.assert_array_equal(out["area"].cpu().numpy().astype(np.uint64), a_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
