@@ -220,8 +220,11 @@ typedef struct {
 /*
  * Batched routing of many independent DEMs of uneven size (receivers +
  * accumulation for every tile) with one launch per stage over all tiles,
- * CTAs taking work from a device-side queue; the sequence can be captured in
- * a CUDA graph.
+ * persistent CTAs taking work from device-side counters; the sequence reads
+ * no host memory when it executes and can be captured in a CUDA graph.  All
+ * tiles must request the same outputs (w_out / area_out set for all or none;
+ * area_out only with FR_ROUTING_D8, w_out required with FR_ROUTING_MFD).
+ * flags: FR_EDGE_* and FR_D8_* (no FR_CHECK_FINITE).
  *   tiles_host  [ntiles] host array (read during the call only).
  *   tiles_dev   [ntiles] device copy of the same array, provided by the
  *               caller (so that no host memory is read at execution time).
@@ -233,6 +236,17 @@ fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, in
                          void* stream);
 size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_t kind,
                                uint32_t flags);
+
+/*
+ * Autotuner of the batched route: runs fr_route_batch with several CTA counts
+ * for its persistent stages (synchronising the stream after each trial) and
+ * keeps the fastest for later fr_route_batch calls of the same kind in this
+ * process.  Same arguments as fr_route_batch; not for use during stream
+ * capture.  The outputs hold a valid result afterwards.
+ */
+fr_status fr_batch_autotune(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
+                            int32_t kind, double p, uint32_t flags, void* ws, size_t ws_bytes,
+                            void* stream);
 
 /* Workspace bytes an operation needs for an nx-by-ny grid (0 if the sizes
  * are invalid).  FR_OP_RECEIVERS needs none. */

@@ -44,6 +44,7 @@ FR_OP_ROUTE = 4
 EXPORTS = (
     "fr_receivers_d8", "fr_receivers_mfd", "fr_accumulate", "fr_route_d8", "fr_route_mfd",
     "fr_route_adjoint", "fr_mass_balance", "fr_route_batch", "fr_batch_workspace_size",
+    "fr_batch_autotune",
     "fr_workspace_size", "fr_get_status", "fr_status_string", "fr_version",
 )
 
@@ -102,6 +103,7 @@ def load(build_if_missing: bool = True):
             "fr_mass_balance": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_batch": (S, [ctypes.POINTER(fr_tile), P, I32, I32, D, U32, P, ctypes.c_size_t, P]),
             "fr_batch_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(fr_tile), I32, I32, U32]),
+            "fr_batch_autotune": (S, [ctypes.POINTER(fr_tile), P, I32, I32, D, U32, P, ctypes.c_size_t, P]),
             "fr_workspace_size": (ctypes.c_size_t, [I32, I64, I64, U32]),
             "fr_get_status": (S, [P, ctypes.c_size_t, P]),
             "fr_status_string": (ctypes.c_char_p, [S]),

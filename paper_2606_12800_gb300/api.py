@@ -230,3 +230,58 @@ class RouteMFD(torch.autograd.Function):
         R = routing_mfd(mask, dem, dx, p, flags)
         dLdr, dLdz = adjoint(R, w, w_lo, dLdw=grad_w.contiguous().float(), want_dz=True)
         return dLdz, dLdr, None, None, None
+
+
+def route_batch(dems, rains=None, kind: str = "d8", dx: float = 30.0, p: float = 1.1,
+                flags: int = 0, want_w: bool = True, want_lo: bool = False,
+                want_area: bool = False, autotune: bool = False):
+    """Routes many independent DEMs (CUDA float32 2-D tensors) with one
+    fr_route_batch call.  Returns a list of dicts (route, w, w_lo, area)."""
+    from ._lib import fr_tile
+    if kind not in ("d8", "mfd"):
+        raise ValueError("kind must be 'd8' or 'mfd'")
+    k = FR_ROUTING_D8 if kind == "d8" else FR_ROUTING_MFD
+    n = len(dems)
+    if n == 0:
+        return []
+    dev = dems[0].device
+    outs, arr = [], (fr_tile * n)()
+    for i, z in enumerate(dems):
+        _check_grid(z, torch.float32, "dem")
+        ny, nx = z.shape
+        r = None if rains is None else rains[i]
+        if r is not None:
+            _check_grid(r, torch.float32, "rain")
+        o = {"route": torch.empty((ny, nx), dtype=torch.uint8, device=dev)}
+        if want_w:
+            o["w"] = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+        if want_lo:
+            o["w_lo"] = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+        if want_area:
+            o["area"] = torch.empty((ny, nx), dtype=torch.int64, device=dev)
+        t = arr[i]
+        t.dem, t.rain = z.data_ptr(), (r.data_ptr() if r is not None else None)
+        t.w_out = o["w"].data_ptr() if want_w else None
+        t.w_lo_out = o["w_lo"].data_ptr() if want_lo else None
+        t.area_out = o["area"].data_ptr() if want_area else None
+        t.route_out = o["route"].data_ptr()
+        t.nx, t.ny, t.dx = nx, ny, dx
+        outs.append(o)
+    raw = bytes(memoryview(arr).cast("B"))
+    tiles_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+    L = load()
+    need = int(L.fr_batch_workspace_size(arr, n, k, flags))
+    if need == 0:
+        raise ValueError("invalid batch")
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    fn = L.fr_batch_autotune if autotune else L.fr_route_batch
+    check(fn(arr, _p(tiles_dev), n, k, p, flags, _p(ws), need, _stream()), "fr_route_batch")
+    outs[0]["_ws"] = ws  # keeps the workspace (and its status word) alive
+    outs[0]["_tiles"] = tiles_dev
+    return outs
+
+
+def batch_status(outs) -> int:
+    """Status word of a route_batch call (synchronises the stream)."""
+    ws = outs[0]["_ws"]
+    return int(load().fr_get_status(_p(ws), ws.numel(), _stream()))

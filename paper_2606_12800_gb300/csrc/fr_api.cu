@@ -290,28 +290,4 @@ fr_status fr_mass_balance(const fr_routing* R, const float* rain, const float* w
                                            (int)blocks, out_dev, (cudaStream_t)stream));
 }
 
-size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_t kind,
-                               uint32_t flags) {
-    (void)tiles_host;
-    (void)ntiles;
-    (void)kind;
-    (void)flags;
-    return 0;
-}
-
-fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
-                         int32_t kind, double p, uint32_t flags, void* ws, size_t ws_bytes,
-                         void* stream) {
-    (void)tiles_host;
-    (void)tiles_dev;
-    (void)ntiles;
-    (void)kind;
-    (void)p;
-    (void)flags;
-    (void)ws;
-    (void)ws_bytes;
-    (void)stream;
-    return FR_ERR_UNSUPPORTED;
-}
-
 }  // extern "C"

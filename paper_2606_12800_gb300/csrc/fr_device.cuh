@@ -7,6 +7,7 @@
 // same bits.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -97,6 +98,20 @@ struct MfdConst {
     float cd_hi, cd_lo;  // 1/(sqrt(2) dx)
     float p;
 };
+
+// Constants of the weight rule for grid spacing dx and exponent p (FP64 on the
+// host or the device, then rounded; both give the same bits).
+__host__ __device__ inline MfdConst make_mfd_const(double dx, double p) {
+    MfdConst m;
+    const double co = 1.0 / dx;
+    const double cd = 1.0 / (sqrt(2.0) * dx);
+    m.co_hi = (float)co;
+    m.co_lo = (float)(co - (double)m.co_hi);
+    m.cd_hi = (float)cd;
+    m.cd_lo = (float)(cd - (double)m.cd_hi);
+    m.p = (float)p;
+    return m;
+}
 
 // u_k = s_k^p for a strictly lower neighbour, s_k = (zc - zn)/d_k.  The drop
 // and the product with 1/d are carried as two-float and the trailing word is

@@ -328,6 +328,77 @@ __device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t sta
     return n;
 }
 
+// D8 forward walker: one step per global cell, all loads of a step issued
+// together (the routing bytes of the 3 x 3 window, the cell's rain, the donors'
+// values; then the receiver's window).  Same semantics as run_walker.
+template <bool W, bool AREA>
+__device__ __noinline__ unsigned long long walker_d8(const Prob& P, int64_t start) {
+    unsigned long long n = 0;
+    int64_t cur = start;
+    int64_t y = cur / P.nx, x = cur - y * P.nx;
+    while (true) {
+        // window of routing bytes: code of neighbour k (0xFF outside the grid)
+        uint8_t nb[8];
+        uint32_t gm = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t xn = x + offx(k), yn = y + offy(k);
+            const bool in = xn >= 0 && yn >= 0 && xn < P.nx && yn < P.ny;
+            gm |= (uint32_t)in << k;
+            nb[k] = in ? rd_rb(P, cur + offi(k, P.nx)) : (uint8_t)0xFF;
+        }
+        const uint8_t own = rd_rb(P, cur);
+        uint32_t dm = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dm |= (uint32_t)(nb[k] == (uint8_t)opp(k)) << k;
+        if constexpr (W) {
+            df v = df_make(P.init ? rd_in(P.init, P, cur, 8) : 1.0f);
+            float hi[8], lo[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                hi[k] = ((dm >> k) & 1u) ? rd_cg(P.out_hi, P, cur + offi(k, P.nx), 11) : 0.0f;
+                lo[k] = ((dm >> k) & 1u) ? rd_cg(P.out_lo, P, cur + offi(k, P.nx), 12) : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((dm >> k) & 1u) v = df_add(v, df{hi[k], lo[k]});
+            wr_f(P.out_hi, P, cur, v.hi, 13);
+            wr_f(P.out_lo, P, cur, v.lo, 14);
+        }
+        if constexpr (AREA) {
+            uint64_t a[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = ((dm >> k) & 1u) ? rd_area(P, cur + offi(k, P.nx)) : 0ull;
+            uint64_t s = 1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s += a[k];
+            wr_area(P, cur, s);
+        }
+        ++n;
+        __threadfence();
+        if (own >= 8 || !((gm >> own) & 1u)) break;
+        const int64_t u = cur + offi(own, P.nx);
+        if (!gbit(P, u)) break;  // solved exactly by its own tile
+        const uint32_t got = cnt_add(P, u, 1u);
+        // global donors of u
+        const int64_t uy = y + offy(own), ux = x + offx(own);
+        uint32_t need = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t xn = ux + offx(k), yn = uy + offy(k);
+            if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
+            const int64_t j = u + offi(k, P.nx);
+            need += (rd_rb(P, j) == (uint8_t)opp(k)) && gbit(P, j);
+        }
+        if (got != need) break;
+        __threadfence();
+        cur = u;
+        x = ux;
+        y = uy;
+    }
+    return n;
+}
+
 __device__ __forceinline__ uint32_t st_get(const uint32_t* st, int c) {
     if (!FR_OK(c, kTileX * kTileY, 20)) return 0x0Fu;
     return (st[c >> 2] >> (8 * (c & 3))) & 0xFFu;
@@ -790,7 +861,9 @@ __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, 
         const int pid = (int)(item >> 40);
         const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
         const Prob& P = probs ? probs[pid] : single;
-        if (g_deps_global<E>(P, cell) == 0) done += run_walker<E>(P, cell);
+        if (g_deps_global<E>(P, cell) != 0) continue;
+        if constexpr (E::kD8Fwd) done += walker_d8<W, AREA>(P, cell);
+        else done += run_walker<E>(P, cell);
     }
     for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
     if (threadIdx.x == 0) s_done = 0;

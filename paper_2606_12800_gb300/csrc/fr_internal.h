@@ -9,7 +9,6 @@
 
 namespace fr {
 
-MfdConst make_mfd_const(double dx, double p);
 
 // Local flow routing (fr_receivers.cu).
 cudaError_t launch_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx,
@@ -52,7 +51,9 @@ struct EngineGlobals {
     unsigned int finished_ctas;      // walker CTAs that have left the kernel
     unsigned int status;             // fr_status of the device-side checks
     unsigned long long glist_count;  // entries in the global-cell list
-    unsigned long long pad[3];
+    unsigned long long recv_next;    // batched receivers: next tile to claim
+    unsigned long long total_cells;  // batched: cells of all problems (set on the device)
+    unsigned long long pad[1];
 };
 static_assert(sizeof(EngineGlobals) == 64, "globals block is 64 bytes");
 
@@ -76,9 +77,15 @@ cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t*
                                 const float* rain, const float* w, const float* w_lo,
                                 const uint64_t* area, double* partials, int nblocks,
                                 double* out, cudaStream_t s);
-cudaError_t launch_receivers_batch(int kind, const Prob* probs_dev, const int64_t* tile_prefix_dev,
-                                   int32_t nprob, int64_t total_tiles, uint32_t flags,
-                                   cudaStream_t s);
+cudaError_t launch_receivers_batch(int kind, const Prob* probs, const int64_t* prefix, int nprob,
+                                   uint32_t flags, EngineGlobals* G, int grid, cudaStream_t s);
+
+// Receiver kernels work on tiles of kRecvTileX x kRecvTileY cells.
+constexpr int kRecvTileX = 128;
+constexpr int kRecvTileY = 16;
+__host__ __device__ inline int64_t receiver_tiles(int64_t nx, int64_t ny) {
+    return ((nx + kRecvTileX - 1) / kRecvTileX) * ((ny + kRecvTileY - 1) / kRecvTileY);
+}
 
 // Engine tile shape (cells): every launch uses the same tile so that the
 // batched and single-grid paths share counters and queues.

@@ -11,22 +11,10 @@
 
 namespace fr {
 
-MfdConst make_mfd_const(double dx, double p) {
-    MfdConst m;
-    double co = 1.0 / dx;
-    double cd = 1.0 / (std::sqrt(2.0) * dx);
-    m.co_hi = (float)co;
-    m.co_lo = (float)(co - (double)m.co_hi);
-    m.cd_hi = (float)cd;
-    m.cd_lo = (float)(cd - (double)m.cd_hi);
-    m.p = (float)p;
-    return m;
-}
-
 namespace {
 
-constexpr int RTX = 128;  // receiver tile width (cells)
-constexpr int RTY = 16;   // receiver tile height
+constexpr int RTX = kRecvTileX;  // receiver tile width (cells)
+constexpr int RTY = kRecvTileY;  // receiver tile height
 constexpr int RNT = 256;  // threads
 constexpr int HX = RTX + 4, HY = RTY + 4;
 constexpr int RX = RTX + 2, RY = RTY + 2;
@@ -62,14 +50,13 @@ __device__ __forceinline__ void tile_origin(int64_t nx, int64_t& x0, int64_t& y0
 // cells of a row from a 3 x 6 register window.  Tiles away from the grid
 // boundary skip all edge and bounds tests.
 template <bool INDEG>
-__global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ z, int64_t nx,
-                                                      int64_t ny, float c_orth, float c_diag,
-                                                      uint32_t flags, uint8_t* __restrict__ dir,
-                                                      uint8_t* __restrict__ indeg) {
+__device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_t nx, int64_t ny,
+                                             float c_orth, float c_diag, uint32_t flags,
+                                             uint8_t* __restrict__ dir,
+                                             uint8_t* __restrict__ indeg, int64_t x0,
+                                             int64_t y0) {
     __shared__ float zs[HX * HY];
     __shared__ uint8_t ds[RX * RY];
-    int64_t x0, y0;
-    tile_origin(nx, x0, y0);
     const bool lowest = flags & kD8Lowest;
     const bool edge_route = flags & kEdgeRoute;
     const bool interior = x0 >= 2 && y0 >= 2 && x0 + RTX + 2 <= nx && y0 + RTY + 2 <= ny;
@@ -148,16 +135,23 @@ __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ 
     }
 }
 
-template <bool FRAC, bool INDEG>
-__global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__ z, int64_t nx,
-                                                       int64_t ny, MfdConst mc, uint32_t flags,
-                                                       uint8_t* __restrict__ mask,
-                                                       float* __restrict__ frac,
-                                                       uint8_t* __restrict__ indeg) {
-    __shared__ float zs[HX * HY];
-    __shared__ uint8_t ms[RX * RY];
+template <bool INDEG>
+__global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ z, int64_t nx,
+                                                      int64_t ny, float c_orth, float c_diag,
+                                                      uint32_t flags, uint8_t* __restrict__ dir,
+                                                      uint8_t* __restrict__ indeg) {
     int64_t x0, y0;
     tile_origin(nx, x0, y0);
+    recv_d8_tile<INDEG>(z, nx, ny, c_orth, c_diag, flags, dir, indeg, x0, y0);
+}
+
+template <bool FRAC, bool INDEG>
+__device__ __forceinline__ void recv_mfd_tile(const float* __restrict__ z, int64_t nx, int64_t ny,
+                                              const MfdConst& mc, uint32_t flags,
+                                              uint8_t* __restrict__ mask, float* __restrict__ frac,
+                                              uint8_t* __restrict__ indeg, int64_t x0, int64_t y0) {
+    __shared__ float zs[HX * HY];
+    __shared__ uint8_t ms[RX * RY];
     load_z_tile(zs, z, nx, ny, x0, y0);
     __syncthreads();
     const bool edge_route = flags & kEdgeRoute;
@@ -220,6 +214,51 @@ __global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__
     }
 }
 
+template <bool FRAC, bool INDEG>
+__global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__ z, int64_t nx,
+                                                       int64_t ny, MfdConst mc, uint32_t flags,
+                                                       uint8_t* __restrict__ mask,
+                                                       float* __restrict__ frac,
+                                                       uint8_t* __restrict__ indeg) {
+    int64_t x0, y0;
+    tile_origin(nx, x0, y0);
+    recv_mfd_tile<FRAC, INDEG>(z, nx, ny, mc, flags, mask, frac, indeg, x0, y0);
+}
+
+// Batched receivers: persistent CTAs claim receiver tiles of any problem.
+// prefix[p] is the first receiver tile of problem p (prefix[nprob] = total).
+__global__ void __launch_bounds__(RNT) k_receivers_batch(int kind, const Prob* __restrict__ probs,
+                                                         const int64_t* __restrict__ prefix,
+                                                         int nprob, uint32_t flags,
+                                                         EngineGlobals* G) {
+    __shared__ int64_t s_work;
+    const int64_t total = prefix[nprob];
+    while (true) {
+        if (threadIdx.x == 0) s_work = (int64_t)atomicAdd(&G->recv_next, 1ull);
+        __syncthreads();
+        const int64_t w = s_work;
+        __syncthreads();
+        if (w >= total) break;
+        int lo = 0, hi = nprob - 1;  // last p with prefix[p] <= w
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const Prob& P = probs[lo];
+        const int64_t lt = w - prefix[lo];
+        const int64_t tiles_x = (P.nx + RTX - 1) / RTX;
+        const int64_t ty = lt / tiles_x, tx = lt - ty * tiles_x;
+        if (kind == 0)
+            recv_d8_tile<false>(P.z, P.nx, P.ny, P.mc.co_hi, P.mc.cd_hi, flags,
+                                const_cast<uint8_t*>(P.rb), nullptr, tx * RTX, ty * RTY);
+        else
+            recv_mfd_tile<false, false>(P.z, P.nx, P.ny, P.mc, flags, const_cast<uint8_t*>(P.rb),
+                                        nullptr, nullptr, tx * RTX, ty * RTY);
+        __syncthreads();
+    }
+}
+
 __global__ void k_count_nonfinite(const float* __restrict__ z, int64_t n,
                                   unsigned long long* count) {
     unsigned long long local = 0;
@@ -258,6 +297,12 @@ cudaError_t launch_receivers_mfd(const float* z, int64_t nx, int64_t ny, double 
     else
         k_receivers_mfd<false, false><<<grid, RNT, 0, s>>>(z, nx, ny, mc, flags, mask, nullptr,
                                                            nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_receivers_batch(int kind, const Prob* probs, const int64_t* prefix, int nprob,
+                                   uint32_t flags, EngineGlobals* G, int grid, cudaStream_t s) {
+    k_receivers_batch<<<grid, RNT, 0, s>>>(kind, probs, prefix, nprob, flags, G);
     return cudaGetLastError();
 }
 

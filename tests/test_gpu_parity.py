@@ -247,3 +247,55 @@ def test_d8_benchmark_workload_full_size(api):
     _, a_ref = oracle.accumulate_d8(d_ref, order, None)
     np.testing.assert_array_equal(out["area"].cpu().numpy().astype(np.uint64), a_ref)
     assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+def _batch_specs():
+    return [(17, 23, 2.0), (64, 64, 1.8), (31, 200, 2.4), (130, 97, 2.1), (300, 257, 2.0),
+            (5, 5, 2.2), (1, 40, 2.0), (90, 1, 2.0), (256, 300, 1.9), (128, 64, 2.3)]
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_route_batch_d8(api, autotune):
+    specs = _batch_specs()
+    dems = [inputs.fractal_dem(ny, nx, beta=b, tilt=0.0, seed=i) for i, (ny, nx, b) in enumerate(specs)]
+    rains = [inputs.rain_field(z.shape[0], z.shape[1], i) for i, z in enumerate(dems)]
+    outs = api.route_batch([cuda(z) for z in dems], [cuda(r) for r in rains], "d8",
+                           want_w=True, want_area=True, autotune=autotune)
+    assert api.batch_status(outs) == 0
+    for z, r, o in zip(dems, rains, outs):
+        d_ref, w_ref, _, order = oracle.route_d8(z, 30.0, r)
+        _, a_ref = oracle.accumulate_d8(d_ref, order, None)
+        np.testing.assert_array_equal(o["route"].cpu().numpy(), d_ref)
+        np.testing.assert_array_equal(o["area"].cpu().numpy().astype(np.uint64), a_ref)
+        assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+def test_route_batch_mfd(api):
+    specs = _batch_specs()
+    dems = [inputs.fractal_dem(ny, nx, beta=b, tilt=0.0, seed=10 + i) for i, (ny, nx, b) in enumerate(specs)]
+    rains = [inputs.rain_field(z.shape[0], z.shape[1], i) for i, z in enumerate(dems)]
+    outs = api.route_batch([cuda(z) for z in dems], [cuda(r) for r in rains], "mfd", p=1.1,
+                           want_w=True, want_lo=True)
+    assert api.batch_status(outs) == 0
+    for z, r, o in zip(dems, rains, outs):
+        m_ref, f_ref, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, r)
+        np.testing.assert_array_equal(o["route"].cpu().numpy(), m_ref)
+        assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+def test_autograd_route_mfd(api):
+    """RouteMFD backward equals the adjoint of the FP64 oracle."""
+    ny, nx = 48, 40
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=5)
+    rain = inputs.rain_field(ny, nx, 5)
+    zt = cuda(z).requires_grad_(True)
+    rt = cuda(rain).requires_grad_(True)
+    w = api.RouteMFD.apply(zt, rt, 30.0, 1.1, 0)
+    gbar = np.random.default_rng(3).random((ny, nx)).astype(np.float32)
+    (w * cuda(gbar)).sum().backward()
+    m_ref, f_ref, w_ref, order = oracle.route_mfd(z, 30.0, 1.1, rain)
+    g_ref = oracle.adjoint(order, w_ref, frac=f_ref, gbar=gbar.astype(np.float64))
+    dz_ref = oracle.mfd_grad_z(z, 30.0, 1.1, f_ref, w_ref, g_ref)
+    assert relerr(rt.grad.cpu().numpy(), g_ref) <= RTOL_W
+    dz = zt.grad.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(dz - dz_ref)) <= 1e-4 * np.abs(dz_ref).max()
