@@ -1,27 +1,29 @@
 // fr_d8.cu -- local phase of D8 forward accumulation over halo-extended tiles.
 //
-// Each CTA owns an inner tile of D8X x D8Y cells and solves the extended
-// region (inner tile plus a D8H-cell halo on every side) exactly in shared
-// memory: the paper's per-subdomain high-to-low solve (Sec. 2.4), with
-// overlapping subdomains.  An inner cell is final unless its upstream basin
-// reaches outside the extended region ("global"); on the synthetic fractal
-// DEMs a 4-cell halo leaves about 0.03 % of the cells global, which the walker
-// kernel of fr_engine.cuh then finishes.  Halo cells are solved only to feed
-// the inner ones and are not written.
+// Each CTA owns an inner tile of TX x TY cells and solves the extended region
+// (inner tile plus an H-cell halo on every side) exactly in shared memory: the
+// paper's per-subdomain high-to-low solve (Sec. 2.4), with overlapping
+// subdomains.  An inner cell is final unless its upstream basin reaches
+// outside the extended region ("global"); on the synthetic fractal DEMs a
+// 4-cell halo leaves about 0.03 % of the cells global, which the walker kernel
+// of fr_engine.cuh then finishes.  Halo cells are solved only to feed the
+// inner ones and are not written.
 //
 // Solve: a cell without donors ("bare", about two thirds of a rough DEM) is
-// final at once.  The other cells are finalised in rounds: each thread keeps a
-// bit mask of its own pending cells and finalises a cell once all of its
-// non-bare in-region donors are final (a topological order, Sec. 3.2), pulling
-// the donors' values in fixed code order (deterministic two-float sums; exact
-// 16-bit local areas).  There are no atomics; the rounds stop when nothing is
-// pending or a round makes no progress (a routing cycle).
+// final at once.  Every other cell waits for its non-bare in-region donors
+// (a count).  Cells with nothing to wait for go to a start list; lanes take
+// starts from it dynamically and walk downstream: a finished cell decrements
+// its receiver's count and the lane that completes it continues there ("last
+// arriver", shared-memory atomics).  Each cell is visited once, donor values
+// are pulled in fixed code order (deterministic two-float sums; exact 16-bit
+// local areas), and a routing cycle simply leaves its cells unvisited.
 //
-// Tiles away from the grid boundary take a vector path: receiver codes arrive
-// as 32-bit words, and the donor masks, bare flags and non-bare donor masks of four
-// consecutive cells are computed together on packed bytes (a byte-permute
-// builds each neighbour vector, an exact zero-byte test compares four codes
-// at once).  Tiles touching the boundary take a scalar path with bounds tests.
+// Tiles away from the grid boundary take a vector path: code and rain rows are
+// copied asynchronously (cp.async) in one batch, and the donor masks, bare
+// flags and counts of four consecutive cells are computed together on packed
+// bytes (a byte-permute builds each neighbour vector, an exact zero-byte test
+// compares four codes at once).  Tiles touching the boundary take a scalar
+// path with bounds tests.
 #include <cuda/atomic>
 
 #include "fr_engine.cuh"
@@ -29,28 +31,38 @@
 namespace fr {
 namespace {
 
-constexpr int D8X = 128, D8Y = 32, D8H = 4;
-constexpr int EX = D8X + 2 * D8H, EY = D8Y + 2 * D8H, NE = EX * EY;  // extended region
-constexpr int RY8 = EY + 2;  // region plus a one-cell ring
-constexpr int CP = EX + 8;   // padded row pitch (bytes) of ring-sized byte arrays
-// Ring coordinates (rx, ry), 0 <= rx < EX + 2, live at byte ry * CP + rx + 3;
-// region cell (ex, ey) is ring cell (ex + 1, ey + 1), byte (ey + 1) * CP + ex + 4,
-// so groups of four region cells starting at ex % 4 == 0 are word aligned.
+constexpr int D8H = 4;
 constexpr int NT8 = 512;
-static_assert(NE < 65536, "local areas are 16-bit");
-static_assert(EX % 4 == 0 && CP % 4 == 0 && D8X % 4 == 0, "four-cell groups");
 
-template <bool W, bool AREA>
+template <int TX_, int TY_>
+struct D8Geo {
+    static constexpr int TX = TX_, TY = TY_, H = D8H;
+    static constexpr int EX = TX + 2 * H, EY = TY + 2 * H, NE = EX * EY;  // extended region
+    static constexpr int RY = EY + 2;  // region plus a one-cell ring
+    static constexpr int CP = EX + 8;  // padded row pitch (bytes) of ring-sized byte arrays
+    // Ring coordinates (rx, ry), 0 <= rx < EX + 2, live at byte ry * CP + rx + 3;
+    // region cell (ex, ey) is ring cell (ex + 1, ey + 1), byte (ey + 1) * CP + ex + 4,
+    // so groups of four region cells starting at ex % 4 == 0 are word aligned.
+    static_assert(NE < 65535, "local areas and indices are 16-bit");
+    static_assert(EX % 4 == 0 && CP % 8 == 0 && TX % 4 == 0, "four-cell groups");
+};
+
+template <class Gm, bool W, bool AREA>
 struct SmemD8 {
+    static constexpr int NE = Gm::NE;
     float vhi[W ? NE : 4];
     float vlo[W ? NE : 4];
     uint16_t area[AREA ? NE : 4];
-    uint32_t st[NE / 4];      // per cell byte: kG once the cell is known to be global
-    uint8_t dm[NE];           // in-region donor mask
-    uint8_t nbdm[NE];         // in-region donors that are not bare
-    uint8_t fin[NE];          // 1 final, 0 pending (0x0F outside the grid)
-    uint8_t code[RY8 * CP];   // receiver codes of region + ring, padded rows
-    uint8_t nbp[RY8 * CP];    // 1 where a region cell has a donor (not bare), padded rows
+    uint16_t tgt[NE];              // in-region receiver index, 0xFFFF if none
+    uint32_t st[NE / 4];           // per cell byte: missing non-bare donors (bits 0-3), kG
+    uint8_t dm[NE];                // in-region donor mask
+    uint8_t fin[NE];               // 1 final (bare or visited), 0 pending, 0x0F outside the grid
+    alignas(16) uint8_t code[Gm::RY * Gm::CP];  // receiver codes of region + ring, padded rows
+    union alignas(16) {
+        uint8_t nbp[Gm::RY * Gm::CP];  // pass A/B: 1 where a region cell is not bare
+        uint16_t starts[NE];           // walks: cells with nothing to wait for
+    };
+    int nstarts, next_start;
     unsigned long long done;
 };
 
@@ -61,6 +73,13 @@ __device__ __forceinline__ uint32_t stget(const uint32_t* st, int c) {
 // 0x80 in each byte of x that is zero, 0 elsewhere (exact, no carries between bytes).
 __device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
     return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+}
+
+// Per-byte population count.
+__device__ __forceinline__ uint32_t popc_bytes(uint32_t x) {
+    x = x - ((x >> 1) & 0x55555555u);
+    x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
+    return (x + (x >> 4)) & 0x0F0F0F0Fu;
 }
 
 // The three 4-byte vectors (left, centre, right neighbours) of a group whose
@@ -88,6 +107,18 @@ __device__ __forceinline__ uint32_t nbr(const Row3& up, const Row3& mid, const R
     }
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Marks one global inner cell (rare): its bit and a list entry.
 __device__ __forceinline__ void mark_one(const Prob& P, EngineGlobals* G, int64_t gi) {
     atomicOr(P.gbits + (gi >> 5), 1u << (gi & 31));
@@ -95,38 +126,73 @@ __device__ __forceinline__ void mark_one(const Prob& P, EngineGlobals* G, int64_
     if (FR_OK((int64_t)slot, P.glist_cap, 17)) P.glist[slot] = (unsigned long long)gi;
 }
 
-template <bool W, bool AREA>
+// Warp-aggregated append of up to four start cells per lane (all lanes call).
+template <class S_>
+__device__ __forceinline__ void push_starts(S_& S, int n, const int (&cells)[4]) {
+    const unsigned lane = threadIdx.x & 31u;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (!total) return;
+    int base = 0;
+    if (lane == 31) base = atomicAdd(&S.nstarts, total);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - n;
+    for (int q = 0; q < n; ++q) S.starts[base + q] = (uint16_t)cells[q];
+}
+
+template <class Gm, bool W, bool AREA>
 __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
+    constexpr int TX = Gm::TX, TY = Gm::TY, H = Gm::H, EX = Gm::EX, EY = Gm::EY, NE = Gm::NE;
+    constexpr int RY = Gm::RY, CP = Gm::CP;
+    using Sm = SmemD8<Gm, W, AREA>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemD8<W, AREA>& S = *reinterpret_cast<SmemD8<W, AREA>*>(smem_raw);
+    Sm& S = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
-    const int64_t tiles_x = (P.nx + D8X - 1) / D8X;
+    const int64_t tiles_x = (P.nx + TX - 1) / TX;
     const int64_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
-    const int64_t x0 = tx * D8X, y0 = ty * D8Y;
+    const int64_t x0 = tx * TX, y0 = ty * TY;
     // ring origin (may be negative) and the grid's extent in ring coordinates
-    const int64_t ox = x0 - D8H - 1, oy = y0 - D8H - 1;
+    const int64_t ox = x0 - H - 1, oy = y0 - H - 1;
     const int gx_hi = (int)(P.nx - ox < EX + 2 ? P.nx - ox : EX + 2);
-    const int gy_hi = (int)(P.ny - oy < RY8 ? P.ny - oy : RY8);
+    const int gy_hi = (int)(P.ny - oy < RY ? P.ny - oy : RY);
     const int gx_lo = (int)(ox < 0 ? -ox : 0), gy_lo = (int)(oy < 0 ? -oy : 0);
-    // vector path: the padded ring rows [x0 - 8, x0 + EX) are inside the grid,
-    // and the arrays allow aligned word / float4 access
-    const bool vec = x0 >= 8 && x0 + EX <= P.nx && oy >= 0 && oy + RY8 <= P.ny &&
-                     (P.nx & 3) == 0 && ((uintptr_t)P.rb & 3) == 0 &&
+    // vector path: the padded ring rows [x0 - H - 4, x0 + EX - H + 4) are inside
+    // the grid, and the arrays allow aligned 8-byte / 16-byte access
+    const bool vec = x0 >= H + 4 && x0 + EX - H + 4 <= P.nx && oy >= 0 && oy + RY <= P.ny &&
+                     (P.nx & 7) == 0 && ((uintptr_t)P.rb & 7) == 0 &&
                      (!W || !P.init || ((uintptr_t)P.init & 15) == 0) &&
                      (!W || ((uintptr_t)P.out_hi & 15) == 0) &&
                      (!AREA || ((uintptr_t)P.area & 15) == 0);
     uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
+    if (tid == 0) {
+        S.nstarts = 0;
+        S.next_start = 0;
+    }
 
     if (vec) {
-        // ---- codes: whole padded rows as words (byte b <-> grid x = x0 - 8 + b)
-        for (int i = tid; i < RY8 * (CP / 4); i += NT8) {
-            const int ry = i / (CP / 4), w = i - ry * (CP / 4);
-            const int64_t g = (oy + ry) * P.nx + (x0 - 8 + 4 * w);
-            reinterpret_cast<uint32_t*>(S.code)[i] =
-                FR_OK(g + 3, ncell(P), 1) ? __ldg(reinterpret_cast<const uint32_t*>(P.rb + g)) : 0xFFFFFFFFu;
+        // ---- asynchronous copies: code rows (8-byte chunks; byte b <-> grid
+        // x = x0 - H - 4 + b) and rain rows (16-byte chunks)
+        for (int i = tid; i < RY * (CP / 8); i += NT8) {
+            const int ry = i / (CP / 8), w = i - ry * (CP / 8);
+            const int64_t g = (oy + ry) * P.nx + (x0 - H - 4 + 8 * w);
+            if (FR_OK(g + 7, ncell(P), 1)) cp_async8(S.code + ry * CP + 8 * w, P.rb + g);
         }
+        if constexpr (W) {
+            if (P.init) {
+                for (int i = tid; i < EY * (EX / 4); i += NT8) {
+                    const int ey = i / (EX / 4), q = i - ey * (EX / 4);
+                    const int64_t g = (oy + ey + 1) * P.nx + (x0 - H + 4 * q);
+                    if (FR_OK(g + 3, ncell(P), 8)) cp_async16(S.vhi + ey * EX + 4 * q, P.init + g);
+                }
+            }
+        }
+        cp_async_wait_all();
         __syncthreads();
-        // ---- donor masks, bare flags, global flags, initial values (4 cells / thread)
+        // ---- donor masks, bare / global flags, receivers (4 cells per thread)
         for (int gq = tid; gq < NE / 4; gq += NT8) {
             const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
             const int w1 = (ex + 4) >> 2;
@@ -149,19 +215,30 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
             reinterpret_cast<uint32_t*>(S.fin)[c >> 2] = bare;
             S.st[c >> 2] = glob;
             reinterpret_cast<uint32_t*>(S.nbp + (ey + 1) * CP)[w1] = bare ^ 0x01010101u;
+            uint32_t t01 = 0, t23 = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t k = (mid.c >> (8 * q)) & 0xFFu;
+                uint32_t t = 0xFFFFu;
+                if (k < 8) {
+                    const int xr = ex + q + offx((int)k), yr = ey + offy((int)k);
+                    if (xr >= 0 && yr >= 0 && xr < EX && yr < EY) t = (uint32_t)(yr * EX + xr);
+                }
+                if (q < 2) t01 |= t << (16 * q);
+                else t23 |= t << (16 * (q - 2));
+            }
+            *reinterpret_cast<uint2*>(S.tgt + c) = make_uint2(t01, t23);
             if constexpr (W) {
-                const int64_t g = (oy + ey + 1) * P.nx + (x0 - D8H + ex);
-                float4 r = make_float4(1.f, 1.f, 1.f, 1.f);
-                if (P.init && FR_OK(g + 3, ncell(P), 8))
-                    r = __ldg(reinterpret_cast<const float4*>(P.init + g));
-                *reinterpret_cast<float4*>(S.vhi + c) = r;
+                if (!P.init) *reinterpret_cast<float4*>(S.vhi + c) = make_float4(1.f, 1.f, 1.f, 1.f);
                 *reinterpret_cast<float4*>(S.vlo + c) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             if constexpr (AREA) *reinterpret_cast<uint2*>(S.area + c) = make_uint2(0x00010001u, 0x00010001u);
         }
         __syncthreads();
-        // ---- non-bare donor masks
-        for (int gq = tid; gq < NE / 4; gq += NT8) {
+        // ---- counts of non-bare in-region donors
+        uint32_t cnts[(NE / 4 + NT8 - 1) / NT8];
+        int nq = 0;
+        for (int gq = tid; gq < NE / 4; gq += NT8, ++nq) {
             const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
             const int c = ey * EX + ex;
             const uint32_t dmr = reinterpret_cast<const uint32_t*>(S.dm)[c >> 2];
@@ -174,12 +251,31 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) nb |= (nbr(up, mid, dn, k) & 0x01010101u) << k;
             }
-            reinterpret_cast<uint32_t*>(S.nbdm)[c >> 2] = nb & dmr;
+            cnts[nq] = popc_bytes(nb & dmr);
+        }
+        __syncthreads();  // nbp is dead from here: its space holds the start list
+        nq = 0;
+        for (int gq0 = 0; gq0 < NE / 4; gq0 += NT8, ++nq) {
+            const int gq = gq0 + tid;
+            int cells[4];
+            int n = 0;
+            if (gq < NE / 4) {
+                const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
+                const int c = ey * EX + ex;
+                const uint32_t cnt = cnts[nq];
+                S.st[c >> 2] |= cnt;
+                const uint32_t fin = reinterpret_cast<const uint32_t*>(S.fin)[c >> 2];
+                const uint32_t st_mask = zero_bytes(fin) & zero_bytes(cnt);  // not bare, no wait
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if ((st_mask >> (8 * q + 7)) & 1u) cells[n++] = c + q;
+            }
+            push_starts(S, n, cells);
         }
         __syncthreads();
     } else {
         // ---- scalar path (tiles touching the grid boundary)
-        for (int i = tid; i < RY8 * CP; i += NT8) {
+        for (int i = tid; i < RY * CP; i += NT8) {
             const int ry = i / CP, rx = i - ry * CP - 3;
             uint8_t code = kSink;
             if (rx >= gx_lo && rx < gx_hi && ry >= gy_lo && ry < gy_hi) {
@@ -197,8 +293,8 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
         for (int c = tid; c < NE; c += NT8) {
             const int ey = c / EX, ex = c - ey * EX;
             const int rx = ex + 1, ry = ey + 1;
-            uint8_t b = 0;
-            uint8_t dmr = 0, bare = 0x0F;  // outside the grid: never solved
+            uint8_t b = 0, dmr = 0, bare = 0x0F;  // outside the grid: never solved
+            uint16_t t = 0xFFFFu;
             if (rx >= gx_lo && rx < gx_hi && ry >= gy_lo && ry < gy_hi) {
                 const int r = ry * CP + rx + 3;
                 uint32_t dm = 0;
@@ -213,6 +309,11 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
                 dmr = (uint8_t)(dm & in);
                 b = (uint8_t)((dm & ~in) ? kG : 0u);
                 bare = dm == 0;
+                const uint8_t k = S.code[r];
+                if (k < 8) {
+                    const int xr = ex + offx(k), yr = ey + offy(k);
+                    if (xr >= 0 && yr >= 0 && xr < EX && yr < EY) t = (uint16_t)(yr * EX + xr);
+                }
                 if constexpr (W) {
                     const int64_t gi = (oy + ry) * P.nx + (ox + rx);
                     S.vhi[c] = P.init ? rd_in(P.init, P, gi, 8) : 1.0f;
@@ -222,94 +323,106 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
             }
             S.dm[c] = dmr;
             S.fin[c] = bare;
+            S.tgt[c] = t;
             stb[c] = b;
         }
         __syncthreads();
-        for (int c = tid; c < NE; c += NT8) {
-            uint32_t nb = 0;
+        uint8_t cnt_own[(NE + NT8 - 1) / NT8];
+        int nq = 0;
+        for (int c = tid; c < NE; c += NT8, ++nq) {
+            uint32_t n = 0;
             for (uint32_t m = S.dm[c]; m; m &= m - 1) {
                 const int k = __ffs(m) - 1;
-                if (S.fin[c + offy(k) * EX + offx(k)] != 1) nb |= 1u << k;
+                n += S.fin[c + offy(k) * EX + offx(k)] != 1;
             }
-            S.nbdm[c] = (uint8_t)nb;
+            cnt_own[nq] = (uint8_t)n;
+        }
+        __syncthreads();
+        nq = 0;
+        for (int c0 = 0; c0 < NE; c0 += NT8, ++nq) {
+            const int c = c0 + tid;
+            int cells[4];
+            int n = 0;
+            if (c < NE) {
+                stb[c] |= cnt_own[nq];
+                if (S.fin[c] == 0 && cnt_own[nq] == 0) cells[n++] = c;
+            }
+            push_starts(S, n, cells);
         }
         __syncthreads();
     }
 
-    // ---- rounds: finalise pending cells whose non-bare donors are final
+    // ---- walks: lanes take start cells dynamically (one claim per warp)
     {
-        constexpr int KMAX = (NE + NT8 - 1) / NT8;
-        static_assert(KMAX <= 32, "pending cells fit a 32-bit mask");
-        uint32_t pend = 0;
-        for (int k = 0; k < KMAX; ++k) {
-            const int c = tid + k * NT8;
-            if (c < NE && S.fin[c] == 0) pend |= 1u << k;
-        }
+        const unsigned lane = tid & 31u;
+        const int nstarts = S.nstarts;
+        int c = -1;
         while (true) {
-            uint32_t progress = 0;
-            for (uint32_t m = pend; m; m &= m - 1) {
-                const int k = __ffs(m) - 1;
-                const int c = tid + k * NT8;
-                const uint32_t nbd = S.nbdm[c];
-                bool ready = true;
-                uint32_t g = stb[c] & kG;
-                for (uint32_t q = nbd; q; q &= q - 1) {
-                    const int j = c + offy(__ffs(q) - 1) * EX + offx(__ffs(q) - 1);
-                    if (reinterpret_cast<volatile uint8_t*>(S.fin)[j] != 1) {
-                        ready = false;
-                        break;
-                    }
-                    g |= stb[j] & kG;
+            const unsigned am = __activemask();
+            const unsigned need = __ballot_sync(am, c < 0);
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                int base = 0;
+                if ((int)lane == leader) base = atomicAdd(&S.next_start, __popc(need));
+                base = __shfl_sync(am, base, leader);
+                if (c < 0) {
+                    const int idx = base + __popc(need & ((1u << lane) - 1u));
+                    if (idx >= nstarts) break;
+                    c = S.starts[idx];
                 }
-                if (!ready) continue;
-                __threadfence_block();  // donors' values are visible once their flags are
-                if (!g) {
-                    const uint32_t dm = S.dm[c];
-                    df v;
-                    uint32_t a = 0;
-                    if constexpr (W) v = {S.vhi[c], S.vlo[c]};
-                    if constexpr (AREA) a = S.area[c];
-                    for (uint32_t q = dm; q; q &= q - 1) {
-                        const int kk = __ffs(q) - 1;
-                        const int j = c + offy(kk) * EX + offx(kk);
-                        if constexpr (W) v = df_add(v, df{S.vhi[j], S.vlo[j]});
-                        if constexpr (AREA) a += S.area[j];
-                    }
-                    if constexpr (W) {
-                        S.vhi[c] = v.hi;
-                        S.vlo[c] = v.lo;
-                    }
-                    if constexpr (AREA) S.area[c] = (uint16_t)a;
-                } else {
-                    stb[c] = (uint8_t)kG;
-                }
-                __threadfence_block();  // publish the value before the flag
-                reinterpret_cast<volatile uint8_t*>(S.fin)[c] = 1;
-                pend &= ~(1u << k);
-                progress = 1;
             }
-            if (!__syncthreads_or(pend != 0)) break;
-            if (!__syncthreads_or(progress)) break;  // a cycle: nothing can finish
+            const uint32_t b = stget(S.st, c);
+            const bool glob = b & kG;
+            const uint32_t dm = S.dm[c];
+            if (!glob && dm) {
+                // pull the donors' values in ascending code order (set bits of dm)
+                df v;
+                uint32_t a = 0;
+                if constexpr (W) v = {S.vhi[c], S.vlo[c]};
+                if constexpr (AREA) a = S.area[c];
+                for (uint32_t m = dm; m; m &= m - 1) {
+                    const int k = __ffs(m) - 1;
+                    const int j = c + offy(k) * EX + offx(k);
+                    if constexpr (W) v = df_add(v, df{S.vhi[j], S.vlo[j]});
+                    if constexpr (AREA) a += S.area[j];
+                }
+                if constexpr (W) {
+                    S.vhi[c] = v.hi;
+                    S.vlo[c] = v.lo;
+                }
+                if constexpr (AREA) S.area[c] = (uint16_t)a;
+            }
+            S.fin[c] = 1;
+            const int t = S.tgt[c];
+            int next = -1;
+            if (t != 0xFFFF) {
+                const uint32_t sh = 8u * (uint32_t)(t & 3);
+                cuda::atomic_ref<uint32_t, cuda::thread_scope_block> word(S.st[t >> 2]);
+                if (glob) word.fetch_or(kG << sh, cuda::memory_order_relaxed);
+                // release this cell's value; acquire the other donors' values
+                const uint32_t old = word.fetch_sub(1u << sh, cuda::memory_order_acq_rel);
+                if (((old >> sh) & 0x0Fu) == 1u) next = t;
+            }
+            c = next;
         }
     }
     __syncthreads();
 
     // ---- inner tile: publish final cells, list global ones
     unsigned long long done = 0;
-    auto need_lo_of = [&](int lx, int ly) -> bool {
+    auto need_lo_of = [&](int c, int lx, int ly) -> bool {
         // a cell's trailing word is pulled later when its receiver leaves the
         // inner tile (another tile may list it as global) or is global here
-        const uint8_t code = S.code[(ly + D8H + 1) * CP + lx + D8H + 4];
+        const uint8_t code = S.code[(ly + H + 1) * CP + lx + H + 4];
         if (code >= 8) return false;
         const int lxr = lx + offx(code), lyr = ly + offy(code);
-        return lxr < 0 || lyr < 0 || lxr >= D8X || lyr >= D8Y ||
-               (stget(S.st, (lyr + D8H) * EX + lxr + D8H) & kG);
+        if (lxr < 0 || lyr < 0 || lxr >= TX || lyr >= TY) return true;
+        return stget(S.st, c + offy(code) * EX + offx(code)) & kG;
     };
     auto publish_one = [&](int lx, int ly) {
-        const int ex = lx + D8H, ey = ly + D8H;
         const int64_t gx = x0 + lx, gy = y0 + ly;
         if (gx >= P.nx || gy >= P.ny) return;
-        const int c = ey * EX + ex;
+        const int c = (ly + H) * EX + lx + H;
         const int64_t gi = gy * P.nx + gx;
         if (stget(S.st, c) & kG) {
             mark_one(P, G, gi);
@@ -319,14 +432,14 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
         ++done;
         if constexpr (W) {
             wr_f(P.out_hi, P, gi, S.vhi[c], 27);
-            if (P.lo_full || need_lo_of(lx, ly)) wr_f(P.out_lo, P, gi, S.vlo[c], 28);
+            if (P.lo_full || need_lo_of(c, lx, ly)) wr_f(P.out_lo, P, gi, S.vlo[c], 28);
         }
         if constexpr (AREA) wr_area(P, gi, S.area[c]);
     };
-    if (vec && x0 + D8X <= P.nx && y0 + D8Y <= P.ny) {
-        for (int gq = tid; gq < D8X * D8Y / 4; gq += NT8) {
-            const int ly = gq / (D8X / 4), lx = (gq - ly * (D8X / 4)) * 4;
-            const int c = (ly + D8H) * EX + lx + D8H;
+    if (vec && x0 + TX <= P.nx && y0 + TY <= P.ny) {
+        for (int gq = tid; gq < TX * TY / 4; gq += NT8) {
+            const int ly = gq / (TX / 4), lx = (gq - ly * (TX / 4)) * 4;
+            const int c = (ly + H) * EX + lx + H;
             const uint32_t st4 = S.st[c >> 2];
             const uint32_t fin4 = reinterpret_cast<const uint32_t*>(S.fin)[c >> 2];
             if ((st4 & 0x10101010u) || fin4 != 0x01010101u) {
@@ -339,7 +452,8 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
                 *reinterpret_cast<float4*>(P.out_hi + gi) = *reinterpret_cast<const float4*>(S.vhi + c);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (P.lo_full || need_lo_of(lx + q, ly)) wr_f(P.out_lo, P, gi + q, S.vlo[c + q], 28);
+                    if (P.lo_full || need_lo_of(c + q, lx + q, ly))
+                        wr_f(P.out_lo, P, gi + q, S.vlo[c + q], 28);
             }
             if constexpr (AREA) {
                 const uint2 a = *reinterpret_cast<const uint2*>(S.area + c);
@@ -349,8 +463,8 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
             }
         }
     } else {
-        for (int i = tid; i < D8X * D8Y; i += NT8) {
-            const int ly = i / D8X, lx = i - ly * D8X;
+        for (int i = tid; i < TX * TY; i += NT8) {
+            const int ly = i / TX, lx = i - ly * TX;
             publish_one(lx, ly);
         }
     }
@@ -362,14 +476,14 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
     if (tid == 0 && S.done) atomicAdd(&G->done_cells, S.done);
 }
 
-template <bool W, bool AREA>
+template <class Gm, bool W, bool AREA>
 cudaError_t launch_d8(const Prob& P, EngineGlobals* G, cudaStream_t s) {
-    constexpr size_t sm = sizeof(SmemD8<W, AREA>);
-    cudaError_t e = cudaFuncSetAttribute(k_local_d8<W, AREA>,
+    constexpr size_t sm = sizeof(SmemD8<Gm, W, AREA>);
+    cudaError_t e = cudaFuncSetAttribute(k_local_d8<Gm, W, AREA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = ((P.nx + D8X - 1) / D8X) * ((P.ny + D8Y - 1) / D8Y);
-    k_local_d8<W, AREA><<<(unsigned)tiles, NT8, sm, s>>>(P, G);
+    const int64_t tiles = ((P.nx + Gm::TX - 1) / Gm::TX) * ((P.ny + Gm::TY - 1) / Gm::TY);
+    k_local_d8<Gm, W, AREA><<<(unsigned)tiles, NT8, sm, s>>>(P, G);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_global<Mode::FwdD8, W, AREA><<<walker_grid(), 256, 0, s>>>(nullptr, P, G,
@@ -377,14 +491,16 @@ cudaError_t launch_d8(const Prob& P, EngineGlobals* G, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+using GeoD8 = D8Geo<128, 32>;
+
 }  // namespace
 
 // D8 forward accumulation: halo-tile local phase + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& P, EngineGlobals* G,
                               cudaStream_t s) {
-    if (want_w && want_area) return launch_d8<true, true>(P, G, s);
-    if (want_w) return launch_d8<true, false>(P, G, s);
-    return launch_d8<false, true>(P, G, s);
+    if (want_w && want_area) return launch_d8<GeoD8, true, true>(P, G, s);
+    if (want_w) return launch_d8<GeoD8, true, false>(P, G, s);
+    return launch_d8<GeoD8, false, true>(P, G, s);
 }
 
 }  // namespace fr

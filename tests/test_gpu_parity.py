@@ -220,7 +220,7 @@ def test_routing_pointing_outside_grid_is_a_sink(api):
     assert api.get_status() == 0
 
 
-@pytest.mark.parametrize("shape,seed", [((2048, 1536), 3), ((1500, 2600), 7)])
+@pytest.mark.parametrize("shape,seed", [((2048, 1536), 3), ((1500, 2600), 7), ((700, 1100), 2)])
 def test_route_d8_large(api, shape, seed):
     """Many tiles: cross-tile chains, halo overlaps and walkers all occur."""
     ny, nx = shape
