@@ -11,12 +11,14 @@
 //
 // Solve: a cell without donors ("bare", about two thirds of a rough DEM) is
 // final at once.  Every other cell waits for its non-bare in-region donors
-// (a count).  Cells with nothing to wait for go to a start list; lanes take
-// starts from it dynamically and walk downstream: a finished cell decrements
-// its receiver's count and the lane that completes it continues there ("last
-// arriver", shared-memory atomics).  Each cell is visited once, donor values
-// are pulled in fixed code order (deterministic two-float sums; exact 16-bit
-// local areas), and a routing cycle simply leaves its cells unvisited.
+// (a count).  The cells are then finalised level by level (a topological
+// order, Sec. 3.2): the first level is every cell with nothing to wait for;
+// each finished cell decrements its receiver's count, and a receiver whose
+// count reaches zero is appended to the next level with one warp-aggregated
+// append.  Every level is a compact list, so all lanes of a warp have work.
+// Each cell is visited once, donor values are pulled in fixed code order
+// (deterministic two-float sums; exact 16-bit local areas), and a routing
+// cycle simply leaves its cells unvisited.
 //
 // Tiles away from the grid boundary take a vector path: code and rain rows are
 // copied asynchronously (cp.async) in one batch, and the donor masks, bare
@@ -58,11 +60,9 @@ struct SmemD8 {
     uint8_t dm[NE];                // in-region donor mask
     uint8_t fin[NE];               // 1 final (bare or visited), 0 pending, 0x0F outside the grid
     alignas(16) uint8_t code[Gm::RY * Gm::CP];  // receiver codes of region + ring, padded rows
-    union alignas(16) {
-        uint8_t nbp[Gm::RY * Gm::CP];  // pass A/B: 1 where a region cell is not bare
-        uint16_t starts[NE];           // walks: cells with nothing to wait for
-    };
-    int nstarts, next_start;
+    alignas(16) uint8_t nbp[Gm::RY * Gm::CP];   // 1 where a region cell is not bare
+    uint16_t queue[NE];            // level lists, appended one after another
+    int qtail;
     unsigned long long done;
 };
 
@@ -126,7 +126,7 @@ __device__ __forceinline__ void mark_one(const Prob& P, EngineGlobals* G, int64_
     if (FR_OK((int64_t)slot, P.glist_cap, 17)) P.glist[slot] = (unsigned long long)gi;
 }
 
-// Warp-aggregated append of up to four start cells per lane (all lanes call).
+// Warp-aggregated append of up to four cells per lane (all lanes call).
 template <class S_>
 __device__ __forceinline__ void push_starts(S_& S, int n, const int (&cells)[4]) {
     const unsigned lane = threadIdx.x & 31u;
@@ -139,9 +139,9 @@ __device__ __forceinline__ void push_starts(S_& S, int n, const int (&cells)[4])
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     if (!total) return;
     int base = 0;
-    if (lane == 31) base = atomicAdd(&S.nstarts, total);
+    if (lane == 31) base = atomicAdd(&S.qtail, total);
     base = __shfl_sync(0xffffffffu, base, 31) + incl - n;
-    for (int q = 0; q < n; ++q) S.starts[base + q] = (uint16_t)cells[q];
+    for (int q = 0; q < n; ++q) S.queue[base + q] = (uint16_t)cells[q];
 }
 
 template <class Gm, bool W, bool AREA>
@@ -168,10 +168,7 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
                      (!W || ((uintptr_t)P.out_hi & 15) == 0) &&
                      (!AREA || ((uintptr_t)P.area & 15) == 0);
     uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
-    if (tid == 0) {
-        S.nstarts = 0;
-        S.next_start = 0;
-    }
+    if (tid == 0) S.qtail = 0;
 
     if (vec) {
         // ---- asynchronous copies: code rows (8-byte chunks; byte b <-> grid
@@ -235,34 +232,25 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
             if constexpr (AREA) *reinterpret_cast<uint2*>(S.area + c) = make_uint2(0x00010001u, 0x00010001u);
         }
         __syncthreads();
-        // ---- counts of non-bare in-region donors
-        uint32_t cnts[(NE / 4 + NT8 - 1) / NT8];
-        int nq = 0;
-        for (int gq = tid; gq < NE / 4; gq += NT8, ++nq) {
-            const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
-            const int c = ey * EX + ex;
-            const uint32_t dmr = reinterpret_cast<const uint32_t*>(S.dm)[c >> 2];
-            uint32_t nb = 0;
-            if (dmr) {
-                const int w1 = (ex + 4) >> 2;
-                const Row3 up = row3(S.nbp + ey * CP, w1);
-                const Row3 mid = row3(S.nbp + (ey + 1) * CP, w1);
-                const Row3 dn = row3(S.nbp + (ey + 2) * CP, w1);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) nb |= (nbr(up, mid, dn, k) & 0x01010101u) << k;
-            }
-            cnts[nq] = popc_bytes(nb & dmr);
-        }
-        __syncthreads();  // nbp is dead from here: its space holds the start list
-        nq = 0;
-        for (int gq0 = 0; gq0 < NE / 4; gq0 += NT8, ++nq) {
+        // ---- counts of non-bare in-region donors; cells with none start level 1
+        for (int gq0 = 0; gq0 < NE / 4; gq0 += NT8) {
             const int gq = gq0 + tid;
             int cells[4];
             int n = 0;
             if (gq < NE / 4) {
                 const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
                 const int c = ey * EX + ex;
-                const uint32_t cnt = cnts[nq];
+                const uint32_t dmr = reinterpret_cast<const uint32_t*>(S.dm)[c >> 2];
+                uint32_t nb = 0;
+                if (dmr) {
+                    const int w1 = (ex + 4) >> 2;
+                    const Row3 up = row3(S.nbp + ey * CP, w1);
+                    const Row3 mid = row3(S.nbp + (ey + 1) * CP, w1);
+                    const Row3 dn = row3(S.nbp + (ey + 2) * CP, w1);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) nb |= (nbr(up, mid, dn, k) & 0x01010101u) << k;
+                }
+                const uint32_t cnt = popc_bytes(nb & dmr);
                 S.st[c >> 2] |= cnt;
                 const uint32_t fin = reinterpret_cast<const uint32_t*>(S.fin)[c >> 2];
                 const uint32_t st_mask = zero_bytes(fin) & zero_bytes(cnt);  // not bare, no wait
@@ -352,61 +340,60 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
         __syncthreads();
     }
 
-    // ---- walks: lanes take start cells dynamically (one claim per warp)
+    // ---- levels: finalise each level's list, collect the next one
     {
         const unsigned lane = tid & 31u;
-        const int nstarts = S.nstarts;
-        int c = -1;
-        while (true) {
-            const unsigned am = __activemask();
-            const unsigned need = __ballot_sync(am, c < 0);
-            if (need) {
-                const int leader = __ffs(need) - 1;
-                int base = 0;
-                if ((int)lane == leader) base = atomicAdd(&S.next_start, __popc(need));
-                base = __shfl_sync(am, base, leader);
-                if (c < 0) {
-                    const int idx = base + __popc(need & ((1u << lane) - 1u));
-                    if (idx >= nstarts) break;
-                    c = S.starts[idx];
+        int lo = 0, hi = S.qtail;
+        while (lo < hi) {
+            for (int base = lo; base < hi; base += NT8) {
+                const int i = base + tid;
+                int push = -1;
+                if (i < hi) {
+                    const int c = S.queue[i];
+                    const bool glob = stget(S.st, c) & kG;
+                    const uint32_t dm = S.dm[c];
+                    const int t = S.tgt[c];
+                    if (!glob && dm) {
+                        // pull the donors' values in ascending code order (set bits of dm)
+                        df v;
+                        uint32_t a = 0;
+                        if constexpr (W) v = {S.vhi[c], S.vlo[c]};
+                        if constexpr (AREA) a = S.area[c];
+                        for (uint32_t m = dm; m; m &= m - 1) {
+                            const int k = __ffs(m) - 1;
+                            const int j = c + offy(k) * EX + offx(k);
+                            if constexpr (W) v = df_add(v, df{S.vhi[j], S.vlo[j]});
+                            if constexpr (AREA) a += S.area[j];
+                        }
+                        if constexpr (W) {
+                            S.vhi[c] = v.hi;
+                            S.vlo[c] = v.lo;
+                        }
+                        if constexpr (AREA) S.area[c] = (uint16_t)a;
+                    }
+                    S.fin[c] = 1;
+                    if (t != 0xFFFF) {
+                        // counts are read only after the level barrier: relaxed atomics
+                        const uint32_t sh = 8u * (uint32_t)(t & 3);
+                        if (glob) atomicOr(&S.st[t >> 2], kG << sh);
+                        const uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
+                        if (((old >> sh) & 0x0Fu) == 1u) push = t;
+                    }
+                }
+                const unsigned pm = __ballot_sync(0xffffffffu, push >= 0);
+                if (pm) {
+                    int b0 = 0;
+                    if (lane == (unsigned)(__ffs(pm) - 1)) b0 = atomicAdd(&S.qtail, __popc(pm));
+                    b0 = __shfl_sync(0xffffffffu, b0, __ffs(pm) - 1);
+                    if (push >= 0) S.queue[b0 + __popc(pm & ((1u << lane) - 1u))] = (uint16_t)push;
                 }
             }
-            const uint32_t b = stget(S.st, c);
-            const bool glob = b & kG;
-            const uint32_t dm = S.dm[c];
-            if (!glob && dm) {
-                // pull the donors' values in ascending code order (set bits of dm)
-                df v;
-                uint32_t a = 0;
-                if constexpr (W) v = {S.vhi[c], S.vlo[c]};
-                if constexpr (AREA) a = S.area[c];
-                for (uint32_t m = dm; m; m &= m - 1) {
-                    const int k = __ffs(m) - 1;
-                    const int j = c + offy(k) * EX + offx(k);
-                    if constexpr (W) v = df_add(v, df{S.vhi[j], S.vlo[j]});
-                    if constexpr (AREA) a += S.area[j];
-                }
-                if constexpr (W) {
-                    S.vhi[c] = v.hi;
-                    S.vlo[c] = v.lo;
-                }
-                if constexpr (AREA) S.area[c] = (uint16_t)a;
-            }
-            S.fin[c] = 1;
-            const int t = S.tgt[c];
-            int next = -1;
-            if (t != 0xFFFF) {
-                const uint32_t sh = 8u * (uint32_t)(t & 3);
-                cuda::atomic_ref<uint32_t, cuda::thread_scope_block> word(S.st[t >> 2]);
-                if (glob) word.fetch_or(kG << sh, cuda::memory_order_relaxed);
-                // release this cell's value; acquire the other donors' values
-                const uint32_t old = word.fetch_sub(1u << sh, cuda::memory_order_acq_rel);
-                if (((old >> sh) & 0x0Fu) == 1u) next = t;
-            }
-            c = next;
+            __syncthreads();  // the level's values and the next list are complete
+            lo = hi;
+            hi = S.qtail;
+            __syncthreads();  // everybody has read the new end before the next appends
         }
     }
-    __syncthreads();
 
     // ---- inner tile: publish final cells, list global ones
     unsigned long long done = 0;
