@@ -167,6 +167,34 @@ fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint3
                       const float* rain, float* w_out, float* w_lo_out, uint64_t* area_out,
                       uint8_t* dir_out, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * fr_route_d8 without a caller-supplied workspace, for callers that cannot
+ * allocate device memory: a plugin host that passes only input and output
+ * buffers, an application whose own pool allocator has reserved the device
+ * memory, or a loop that cannot take cudaMalloc/cudaFree's implicit device
+ * synchronisation.  The paper has no counterpart; this is an interface
+ * convenience of this library.
+ *   Arguments, outputs and results as fr_route_d8 (all data pointers are
+ *   device pointers; dir_out may be NULL).
+ *   Limit: nx*ny <= FR_NOALLOC_MAX_CELLS; larger grids return
+ *   FR_ERR_INVALID_ARG before any device work.
+ *   Scratch: one file-scope device array of about 22 bytes per cell of that
+ *   limit (about 23 MB), which every GPU that loads the library holds until
+ *   the process exits.  The first call on a device looks up the array's
+ *   address there (cudaGetSymbolAddress, with that device current); make that
+ *   first call before any stream capture.  No call allocates or frees device
+ *   memory.
+ *   Sharing: every call on a device uses the same array and finds the last
+ *   call's contents in it; the parts that must start at zero are cleared on
+ *   the caller's stream at the start of each call.  Calls whose GPU work
+ *   overlaps (different streams, or different host threads on one device)
+ *   race on the array and give wrong results; serialise them.
+ */
+#define FR_NOALLOC_MAX_CELLS ((int64_t)1 << 20)
+fr_status fr_route_d8_noalloc(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
+                              const float* rain, float* w_out, float* w_lo_out,
+                              uint64_t* area_out, uint8_t* dir_out, void* stream);
+
 /* Receivers + accumulation in one call (MFD).  mask_out may be NULL. */
 fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
                        uint32_t flags, const float* rain, float* w_out, float* w_lo_out,

@@ -40,11 +40,14 @@ FR_OP_ADJOINT = 2
 FR_OP_MASS_BALANCE = 3
 FR_OP_ROUTE = 4
 
+# Largest grid (cells) fr_route_d8_noalloc accepts.
+FR_NOALLOC_MAX_CELLS = 1 << 20
+
 # Every symbol include/fr.h declares (checked by the test-suite).
 EXPORTS = (
     "fr_receivers_d8", "fr_receivers_mfd", "fr_accumulate", "fr_route_d8", "fr_route_mfd",
     "fr_route_adjoint", "fr_mass_balance", "fr_route_batch", "fr_batch_workspace_size",
-    "fr_batch_autotune",
+    "fr_batch_autotune", "fr_route_d8_noalloc",
     "fr_workspace_size", "fr_get_status", "fr_status_string", "fr_version",
 )
 
@@ -99,6 +102,7 @@ def load(build_if_missing: bool = True):
             "fr_accumulate": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_d8": (S, [P, I64, I64, D, U32, P, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_mfd": (S, [P, I64, I64, D, D, U32, P, P, P, P, P, ctypes.c_size_t, P]),
+            "fr_route_d8_noalloc": (S, [P, I64, I64, D, U32, P, P, P, P, P, P]),
             "fr_route_adjoint": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_mass_balance": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_batch": (S, [ctypes.POINTER(fr_tile), P, I32, I32, D, U32, P, ctypes.c_size_t, P]),
