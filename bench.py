@@ -38,6 +38,10 @@ N_SIDE = 4096
 MFD_SIDE = 8192
 DX = 30.0
 SEED = 1
+# DRAM bytes (read + write) of one k_local_d8 launch on the 4096^2 workload, from
+# an ncu capture of this kernel as it stands (profiles/k_local_d8_4096.md);
+# None whenever the kernel changes until it is captured again.
+TRAFFIC_K_LOCAL_D8 = 91.644928e6 + 151.898880e6
 
 
 def parse():
@@ -298,9 +302,11 @@ def main():
                    "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas"},
         "phases_ms": {"receivers": statistics.mean(recv_ms), "accumulate": statistics.mean(acc_ms),
                       "mass_balance": statistics.mean(mb_ms)},
-        "roofline": {"bound": "hbm", "kernel": "accumulate (k_engine, FwdD8)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": None, "algorithmic_bytes_per_cell": 17,
+        "roofline": {"bound": "hbm", "kernel": "fr_accumulate D8 (k_local_d8 + k_global)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": TRAFFIC_K_LOCAL_D8,
+                     "traffic_note": "ncu dram read+write of k_local_d8, one launch at this size",
+                     "algorithmic_bytes_per_cell": 17,
                      "step_frac": step_bytes / (total_ms / K * 1e-3) / 1e9 / peak},
         "e2e": e2e,
         "gpu_launches": K * 5,
