@@ -202,7 +202,7 @@ fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, fl
     EngineGlobals* G = reinterpret_cast<EngineGlobals*>(ws);
     if (R->kind == FR_ROUTING_D8)
         return cuda_status(launch_d8_forward(w_out != nullptr, area_out != nullptr, P, G, s));
-    return cuda_status(launch_engine(Mode::FwdMfd, true, false, P, G, s));
+    return cuda_status(launch_mfd_forward(P, G, s));
 }
 
 fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,

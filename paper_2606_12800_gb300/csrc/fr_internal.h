@@ -69,6 +69,8 @@ cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Pr
                                 EngineGlobals* g, int grid, cudaStream_t s);
 int walker_grid();
 // D8 forward: halo-tile local phase (fr_d8.cu) + walker phase.
+// MFD forward accumulation: halo-tile local phase + walker phase (fr_mfd.cu).
+cudaError_t launch_mfd_forward(const Prob& prob, EngineGlobals* g, cudaStream_t s);
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
                               cudaStream_t s);
 cudaError_t launch_mfd_grad_z(const Prob& prob, const float* g_hi, const float* g_lo,

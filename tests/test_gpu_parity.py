@@ -249,6 +249,39 @@ def test_d8_benchmark_workload_full_size(api):
     assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
 
 
+@pytest.mark.parametrize("shape", [(777, 1333), (1024, 1536)])
+def test_route_mfd_walker_without_trailing_words(api, shape):
+    """Grids of many extended tiles, so some cells are finished by the walker
+    kernel, which then reads the trailing words the tiles keep in the
+    workspace (none are requested by the caller)."""
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=ny + 7)
+    rain = inputs.rain_field(ny, nx, 5)
+    out = api.route_mfd(cuda(z), 30.0, 1.1, cuda(rain), 0)
+    assert api.get_status() == 0
+    _, _, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, rain)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    # unit rain as well
+    out = api.route_mfd(cuda(z), 30.0, 1.1, None, 0)
+    _, _, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, None)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+@pytest.mark.slow
+def test_slope_split_full_size_workload(api):
+    """The 8192^2 slope-split workload (beta 2.2, no tilt, unit rain, p = 1.1),
+    generated on the device as the benchmark does: masks bit-exact and water
+    within 1e-6 of the full FP64 oracle, per cell."""
+    n = 8192
+    zt = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=3, device="cuda")
+    out = api.route_mfd(zt, 30.0, 1.1, None, 0, want_mask=True)
+    assert api.get_status() == 0
+    z = zt.cpu().numpy()
+    m_ref, _, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, None)
+    np.testing.assert_array_equal(out["mask"].cpu().numpy(), m_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
 def _batch_specs():
     return [(17, 23, 2.0), (64, 64, 1.8), (31, 200, 2.4), (130, 97, 2.1), (300, 257, 2.0),
             (5, 5, 2.2), (1, 40, 2.0), (90, 1, 2.0), (256, 300, 1.9), (128, 64, 2.3)]
