@@ -16,8 +16,7 @@ cudaError_t launch_single(const Prob& P, EngineGlobals* G, cudaStream_t s) {
     k_local<M, W, A><<<(unsigned)tiles, 256, sm, s>>>(P, G);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_global<M, W, A><<<walker_grid(), 256, 0, s>>>(nullptr, P, G, (unsigned long long)(P.nx * P.ny));
-    return cudaGetLastError();
+    return launch_global<M, W, A>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
 }
 
 template <Mode M, bool W, bool A>
@@ -32,8 +31,7 @@ cudaError_t launch_batch(const Prob* probs, const int64_t* prefix, int nprob, in
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     Prob none{};
-    k_global<M, W, A><<<walker_grid(), 256, 0, s>>>(probs, none, G, total_cells);
-    return cudaGetLastError();
+    return launch_global<M, W, A>(probs, none, G, total_cells, s);
 }
 
 // ---------------------------------------------------------------- mass balance

@@ -68,6 +68,29 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     return df_norm(p, e);
 }
 
+// Sum of eight two-float terms in a fixed pairwise order:
+// ((t0 + t1) + (t2 + t3)) + ((t4 + t5) + (t6 + t7)).  Absent terms are zero,
+// which df_add passes through exactly.  The MFD kernels sum over the eight
+// directions in this order wherever they run (eight lanes with shuffles, or
+// one thread), so a cell's value does not depend on which kernel computed it.
+__device__ __forceinline__ df df_tree8(const df (&t)[8]) {
+    const df a = df_add(df_add(t[0], t[1]), df_add(t[2], t[3]));
+    const df b = df_add(df_add(t[4], t[5]), df_add(t[6], t[7]));
+    return df_add(a, b);
+}
+
+// The same sum across the eight lanes of an aligned group (lane & 7 = term
+// index); every lane of the group returns the total.
+__device__ __forceinline__ df df_tree8_lanes(df t) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const df u = {__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+        t = (lane & (unsigned)o) ? df_add(u, t) : df_add(t, u);
+    }
+    return t;
+}
+
 // ------------------------------------------------------------ D8 predicate
 // zn[k] = elevation of neighbour k, +inf where the neighbour lies outside the
 // grid (never strictly lower).  Strictly lower neighbours only; the largest
@@ -92,11 +115,15 @@ __device__ __forceinline__ uint8_t d8_code(float zc, const float (&zn)[8], float
 }
 
 // ------------------------------------------------------------ MFD weights
-// Reciprocal distances 1/d_k as two-float, set on the host from FP64.
+// Reciprocal distances 1/d_k as two-float, set on the host from FP64, and the
+// exponent p split into its integer part pn and fraction pf (FP64, then
+// rounded), so that s^p = s^pn * 2^(pf log2 s).
 struct MfdConst {
     float co_hi, co_lo;  // 1/dx
     float cd_hi, cd_lo;  // 1/(sqrt(2) dx)
-    float p;
+    float p;             // p rounded to fp32 (used for the first-order corrections)
+    float pf;            // p - floor(p), rounded to fp32
+    int pn;              // floor(p)
 };
 
 // Constants of the weight rule for grid spacing dx and exponent p (FP64 on the
@@ -110,12 +137,56 @@ __host__ __device__ inline MfdConst make_mfd_const(double dx, double p) {
     m.cd_hi = (float)cd;
     m.cd_lo = (float)(cd - (double)m.cd_hi);
     m.p = (float)p;
+    const double pn = floor(p);
+    m.pn = (int)pn;
+    m.pf = (float)(p - pn);
     return m;
+}
+
+// s^p for a positive normal s: s^pn (repeated products) times 2^(pf log2 s).
+// log2 s = e + log2(m) from the exponent e and a mantissa m in [1/sqrt2, sqrt2]
+// (hardware log2, absolute error at most 2^-22 there); pf * e is kept exact as
+// a two-float (FMA); the power of two is split into an integer k and a rest
+// |x| <= ln2/2, and e^x is summed as its Taylor series to degree 7 (truncation
+// below 6e-9).  Relative error about 1e-7 for p in [1, 2], independent of the
+// magnitude of s.  Other s (zero, subnormal, infinite, NaN) fall back to powf.
+__device__ __forceinline__ float mfd_pow(float s, const MfdConst& c) {
+    if (!(s >= 1.17549435e-38f && s <= 3.0e38f)) return powf(s, c.p);
+    const int bits = __float_as_int(s);
+    int e = ((bits >> 23) & 0xFF) - 127;
+    float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+    if (m > 1.41421356f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float fe = (float)e;
+    const float a = __fmul_rn(c.pf, fe);
+    const float ae = __fmaf_rn(c.pf, fe, -a);
+    const float b = __fmul_rn(c.pf, __log2f(m));
+    float k = rintf(a);
+    float r = __fadd_rn(__fadd_rn(__fsub_rn(a, k), b), ae);
+    const float k2 = rintf(r);
+    r = __fsub_rn(r, k2);
+    k = __fadd_rn(k, k2);
+    const float x = __fmul_rn(r, 0.693147180559945309f);
+    float q = __fmaf_rn(x, 1.0f / 5040.0f, 1.0f / 720.0f);
+    q = __fmaf_rn(x, q, 1.0f / 120.0f);
+    q = __fmaf_rn(x, q, 1.0f / 24.0f);
+    q = __fmaf_rn(x, q, 1.0f / 6.0f);
+    q = __fmaf_rn(x, q, 0.5f);
+    q = __fmaf_rn(x, q, 1.0f);
+    q = __fmaf_rn(x, q, 1.0f);
+    float y = __fmul_rn(q, __int_as_float(((int)k + 127) << 23));
+#pragma unroll 1
+    for (int i = 0; i < c.pn; ++i) y = __fmul_rn(y, s);
+    return y;
 }
 
 // u_k = s_k^p for a strictly lower neighbour, s_k = (zc - zn)/d_k.  The drop
 // and the product with 1/d are carried as two-float and the trailing word is
-// applied as a first-order correction of the power: (s+e)^p ~ s^p (1 + p e/s).
+// applied as a first-order correction of the power: (s+e)^p ~ s^p (1 + p e/s)
+// (the quotient e/s only scales a correction of relative size 1e-7, so a
+// fast division suffices).
 __device__ __forceinline__ float mfd_u(float zc, float zn, int k, const MfdConst& m) {
     float dz = __fsub_rn(zc, zn);
     float bb = __fsub_rn(dz, zc);
@@ -126,8 +197,8 @@ __device__ __forceinline__ float mfd_u(float zc, float zn, int k, const MfdConst
     float se = __fmaf_rn(dz, ch, -s);
     se = __fmaf_rn(dz, cl, se);
     se = __fmaf_rn(dze, ch, se);
-    float u = powf(s, m.p);
-    float corr = __fmul_rn(m.p, __fdiv_rn(se, s));
+    float u = mfd_pow(s, m);
+    float corr = __fmul_rn(m.p, __fdividef(se, s));
     return __fmaf_rn(u, corr, u);
 }
 

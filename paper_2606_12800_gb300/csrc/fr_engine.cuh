@@ -165,15 +165,17 @@ __device__ __forceinline__ uint32_t g_targets(const Prob& P, int64_t i) {
 // Inverse normaliser 1/S of cell i's own outflow (MFD), from global memory.
 template <class E>
 __device__ __noinline__ df g_inv_norm(const Prob& P, int64_t i) {
-    uint32_t m = g_recv_own<E>(P, i);
-    int64_t y = i / P.nx, x = i - y * P.nx;
-    float zc = rd_z(P, i);
-    df s = df_make(0.0f);
-#pragma unroll 1
+    const uint32_t m = g_recv_own<E>(P, i);
+    const float zc = rd_z(P, i);
+    // the neighbours' elevations are loaded side by side, then summed in code order
+    float zn[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) zn[k] = ((m >> k) & 1u) ? rd_z(P, i + offi(k, P.nx)) : 0.0f;
+    df t[8];
+#pragma unroll
     for (int k = 0; k < 8; ++k)
-        if ((m >> k) & 1u)
-            s = df_add(s, df_make(mfd_u_call(zc, rd_z(P, i + offi(k, P.nx)), k, P.mc)));
-    return df_recip(s);
+        t[k] = ((m >> k) & 1u) ? df_make(mfd_u_call(zc, zn[k], k, P.mc)) : df_make(0.0f);
+    return df_recip(df_tree8(t));
 }
 
 // Initial value of a cell: rain (forward) or gbar (adjoint).
@@ -220,16 +222,30 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
             }
         } else {
             float zc = E::kMfd ? rd_z(P, t) : 0.0f;
+            // routing bytes of the eight neighbours, loaded side by side
+            const uint32_t gm = grid_mask(x, y, P.nx, P.ny);
+            uint32_t dmask = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((gm >> k) & 1u) dmask |= ((g_recv<E>(P, t + offi(k, P.nx)) >> opp(k)) & 1u) << k;
+            if constexpr (E::kMfd) {
+                // donor terms in the fixed pairwise order of df_tree8
+                df term[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    term[k] = df_make(0.0f);
+                    if (!((dmask >> k) & 1u)) continue;
+                    const int64_t j = t + offi(k, P.nx);
+                    const df wj = g_value<E>(P, j);
+                    term[k] = df_mul(mfd_frac(mfd_u_call(rd_z(P, j), zc, opp(k), P.mc), g_inv_norm<E>(P, j)), wj);
+                }
+                v = df_add(v, df_tree8(term));
+            } else {
 #pragma unroll 1
-            for (int k = 0; k < 8; ++k) {
-                int64_t xn = x + (int64_t)offx(k), yn = y + (int64_t)offy(k);
-                if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
-                int64_t j = yn * P.nx + xn;
-                if (!((g_recv<E>(P, j) >> opp(k)) & 1u)) continue;
-                df wj = g_value<E>(P, j);
-                if constexpr (E::kMfd)
-                    wj = df_mul(mfd_frac(mfd_u_call(rd_z(P, j), zc, opp(k), P.mc), g_inv_norm<E>(P, j)), wj);
-                v = df_add(v, wj);
+                for (int k = 0; k < 8; ++k) {
+                    if (!((dmask >> k) & 1u)) continue;
+                    v = df_add(v, g_value<E>(P, t + offi(k, P.nx)));
+                }
             }
         }
         if (P.out_hi) wr_f(P.out_hi, P, t, v.hi, 13);
@@ -260,7 +276,7 @@ template <class E>
 __device__ __forceinline__ uint32_t g_deps_global(const Prob& P, int64_t i) {
     const uint32_t dep = g_deps<E>(P, i);
     uint32_t n = 0;
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((dep >> k) & 1u) n += gbit(P, i + offi(k, P.nx));
     return n;
@@ -879,6 +895,194 @@ __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, 
             unsigned long long got = atomicAdd(&G->done_cells, 0ull);
             if (got != total_cells) atomicMax(&G->status, kStatusNoProgress);
         }
+    }
+}
+
+// ---------------------------------------------------- level-synchronous global phase
+// For the modes where a finished cell can make several cells ready (MFD
+// forward; both adjoints) a walker that kept every extra ready cell to itself
+// would run whole diverging regions on one thread.  Here the global cells are
+// processed in rounds instead: round r computes every global cell whose global
+// dependencies were all computed in earlier rounds (the frontier), and every
+// cell that becomes ready goes to the next frontier.  The number of rounds is
+// the length of the longest dependency chain among global cells (about 20 on
+// the rough test DEMs).  Before the first round each global cell's arrival
+// counter is set to kReadyAt minus its number of global dependencies, so
+// readiness is a single atomic.  Rounds are separated by a grid barrier
+// (cooperative launch, so all blocks are resident); the barrier's wait is
+// bounded in time.
+
+constexpr unsigned long long kBarrierLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
+constexpr uint32_t kReadyAt = 16u;  // > 8 dependencies, < 256 (one counter byte)
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier over all blocks of a cooperative launch.  Returns false (and leaves
+// FR_ERR_NO_PROGRESS in the status word) if the wait exceeds the time limit.
+static __device__ __noinline__ bool grid_barrier(EngineGlobals* G) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire_u32(&G->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&G->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&G->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&G->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(&G->bar_gen) == gen) {
+                __nanosleep(64);
+                if (global_ns() - t0 > kBarrierLimitNs) {
+                    atomicMax(&G->status, kStatusNoProgress);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Computes one ready global cell and appends the targets it makes ready.
+template <class E>
+__device__ __noinline__ void step_round(const Prob& P, int64_t cur, unsigned long long pid_bits,
+                                        unsigned long long* nxt, unsigned long long* ncount,
+                                        unsigned long long cap) {
+    walker_compute<E>(P, cur);
+    __threadfence();
+    const uint32_t tm = g_targets<E>(P, cur);
+    uint32_t gm = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if ((tm >> k) & 1u) gm |= (uint32_t)gbit(P, cur + offi(k, P.nx)) << k;
+    uint32_t ready = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if ((gm >> k) & 1u) ready |= (uint32_t)(cnt_add(P, cur + offi(k, P.nx), 1u) == kReadyAt) << k;
+    for (; ready; ready &= ready - 1) {
+        const int k = __ffs(ready) - 1;
+        const unsigned long long slot = atomicAdd(ncount, 1ull);
+        if (FR_OK((int64_t)slot, (int64_t)cap, 18))
+            nxt[slot] = pid_bits | (unsigned long long)(cur + offi(k, P.nx));
+    }
+}
+
+// Frontier buffers: the walker-link region (first problem's link array; the
+// links of all problems are contiguous) and the global-cell list, which is
+// free once the first frontier has been built from it.
+template <Mode M, bool W, bool AREA>
+__global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ probs, Prob single,
+                                                       EngineGlobals* G,
+                                                       unsigned long long total_cells) {
+    using E = Eng<M, W, AREA>;
+    __shared__ unsigned long long s_done;
+    const Prob& P0 = probs ? probs[0] : single;
+    unsigned long long* const buf_a = reinterpret_cast<unsigned long long*>(P0.link);
+    unsigned long long* const buf_b = P0.glist;
+    const unsigned long long cap = (unsigned long long)P0.glist_cap;
+    const unsigned long long count = __ldcg(&G->glist_count);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr unsigned long long kCellMask = (1ull << 40) - 1;
+    unsigned long long done = 0;
+    // first frontier: global cells without global dependencies; the others'
+    // counters start at kReadyAt - dependencies
+    for (unsigned long long i = first; i < count; i += stride) {
+        const unsigned long long item = __ldcg(buf_b + i);
+        const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+        const int64_t cell = (int64_t)(item & kCellMask);
+        const uint32_t deps = g_deps_global<E>(P, cell);
+        if (deps) {
+            cnt_add(P, cell, kReadyAt - deps);
+            continue;
+        }
+        const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
+        if (FR_OK((int64_t)slot, (int64_t)cap, 18)) buf_a[slot] = item;
+    }
+    bool ok = grid_barrier(G);
+    for (int round = 1; ok; ++round) {
+        unsigned long long* cur = (round & 1) ? buf_a : buf_b;
+        unsigned long long* nxt = (round & 1) ? buf_b : buf_a;
+        const unsigned long long n = __ldcg(&G->fcount[(round - 1) % 3]);
+        if (n == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) G->rounds = (unsigned long long)(round - 1);
+            break;
+        }
+        // the counter two rounds back is free again: it becomes the next round's
+        if (blockIdx.x == 0 && threadIdx.x == 0) G->fcount[(round + 1) % 3] = 0ull;
+        unsigned long long* ncount = &G->fcount[round % 3];
+        for (unsigned long long i = first; i < n; i += stride) {
+            const unsigned long long item = __ldcg(cur + i);
+            const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+            step_round<E>(P, (int64_t)(item & kCellMask), item & ~kCellMask, nxt, ncount, cap);
+            ++done;
+        }
+        ok = grid_barrier(G);
+    }
+    for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
+    if (threadIdx.x == 0) s_done = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && done) atomicAdd(&s_done, done);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_done) atomicAdd(&G->done_cells, s_done);
+        __threadfence();
+        const unsigned fin = atomicAdd(&G->finished_ctas, 1u);
+        if (fin == gridDim.x - 1) {
+            __threadfence();
+            const unsigned long long got = atomicAdd(&G->done_cells, 0ull);
+            if (got != total_cells) atomicMax(&G->status, kStatusNoProgress);
+        }
+    }
+}
+
+// Launches the global phase: D8 forward keeps the single-successor walkers
+// (a D8 cell has one receiver, so nothing diverges); every other mode runs
+// the level-synchronous kernel as a cooperative launch.
+template <Mode M, bool W, bool AREA>
+cudaError_t launch_global(const Prob* probs, const Prob& single, EngineGlobals* G,
+                          unsigned long long total_cells, cudaStream_t s) {
+    if constexpr (M == Mode::FwdD8) {
+        k_global<M, W, AREA><<<walker_grid(), 256, 0, s>>>(probs, single, G, total_cells);
+        return cudaGetLastError();
+    } else {
+        static int grid_of[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        int grid = dev < 64 ? grid_of[dev] : 0;
+        if (grid == 0) {
+            int sms = 0, per = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_global_levels<M, W, AREA>, 256, 0);
+            if (e != cudaSuccess) return e;
+            if (per < 1) return cudaErrorInvalidConfiguration;
+            grid = sms * (per < 4 ? per : 4);
+            if (dev < 64) grid_of[dev] = grid;
+        }
+        Prob one = single;
+        const Prob* pp = probs;
+        unsigned long long total = total_cells;
+        void* args[] = {(void*)&pp, (void*)&one, (void*)&G, (void*)&total};
+        return cudaLaunchCooperativeKernel((const void*)k_global_levels<M, W, AREA>, dim3(grid),
+                                           dim3(256), args, 0, s);
     }
 }
 

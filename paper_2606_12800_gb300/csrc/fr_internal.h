@@ -53,9 +53,13 @@ struct EngineGlobals {
     unsigned long long glist_count;  // entries in the global-cell list
     unsigned long long recv_next;    // batched receivers: next tile to claim
     unsigned long long total_cells;  // batched: cells of all problems (set on the device)
-    unsigned long long pad[1];
+    unsigned long long fcount[3];    // level-synchronous global phase: frontier sizes
+    unsigned int bar_count;          // grid barrier: blocks arrived
+    unsigned int bar_gen;            // grid barrier: generation
+    unsigned long long rounds;       // level-synchronous global phase: rounds run (diagnostic)
+    unsigned long long pad[4];
 };
-static_assert(sizeof(EngineGlobals) == 64, "globals block is 64 bytes");
+static_assert(sizeof(EngineGlobals) == 128, "globals block is 128 bytes (256 reserved)");
 
 enum class Mode : int { FwdD8 = 0, FwdMfd = 1, AdjD8 = 2, AdjMfd = 3 };
 

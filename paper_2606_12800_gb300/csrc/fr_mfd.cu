@@ -11,13 +11,16 @@
 //
 // Per cell the kernel keeps the elevation (for the weights), the inverse of
 // its weight sum 1/S = 1/sum_k s_k^p as two-float, and its water as two-float.
-// A cell pulls from its donors j in fixed code order:
+// A cell pulls from its donors j:
 //     w_c = r_c + sum_j (u_{j->c} / S_j) w_j,   u = s^p  (App. A),
-// recomputing u_{j->c} from the two elevations, exactly as the walker kernel
+// recomputing u_{j->c} from the two elevations, and sums the eight direction
+// terms in the fixed pairwise order of df_tree8, exactly as the walker kernel
 // does, so a cell's value does not depend on which kernel computed it.
 // Cells are finalised level by level from compact lists (a topological order,
 // Sec. 3.2); a finished cell decrements the counts of all its in-region
-// receivers.
+// receivers.  Eight lanes serve one cell, one per direction (weights, donor
+// terms, receiver updates), so a level of a few dozen cells still keeps the
+// warps of the block busy and its critical path is one weight, not eight.
 #include "fr_engine.cuh"
 
 namespace fr {
@@ -25,6 +28,7 @@ namespace {
 
 constexpr int kMfdTX = 64, kMfdTY = 32, kMfdH = 8;
 constexpr int kMfdNT = 512;
+constexpr int NG = kMfdNT / 8;  // cells served at once (eight lanes each)
 
 struct MfdGeo {
     static constexpr int TX = kMfdTX, TY = kMfdTY, H = kMfdH;
@@ -32,7 +36,18 @@ struct MfdGeo {
     static constexpr int RX = EX + 2, RY = EY + 2, NR = RX * RY;         // plus a one-cell ring
     static_assert(NE < 65535, "local indices are 16-bit");
     static_assert(NE % 4 == 0, "state bytes are packed four to a word");
+    static_assert(NE % NG == 0, "whole passes of eight-lane groups");
 };
+
+// Directions whose neighbour of region cell (ex, ey) lies inside the region.
+__device__ __forceinline__ uint32_t region_mask(int ex, int ey) {
+    uint32_t in = 0xFFu;
+    if (ex == 0) in &= ~0x64u;                // W NW SW
+    if (ex == MfdGeo::EX - 1) in &= ~0x91u;   // E NE SE
+    if (ey == 0) in &= ~0x32u;                // N NE NW
+    if (ey == MfdGeo::EY - 1) in &= ~0xC8u;   // S SW SE
+    return in;
+}
 
 struct SmemMfd {
     static constexpr int NE = MfdGeo::NE, NR = MfdGeo::NR;
@@ -74,7 +89,7 @@ __device__ __forceinline__ void push_cell(SmemMfd& S, int cell) {
 
 __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* G) {
     constexpr int TX = MfdGeo::TX, TY = MfdGeo::TY, H = MfdGeo::H;
-    constexpr int EX = MfdGeo::EX, EY = MfdGeo::EY, NE = MfdGeo::NE;
+    constexpr int EX = MfdGeo::EX, NE = MfdGeo::NE;
     constexpr int RX = MfdGeo::RX, NR = MfdGeo::NR;
     constexpr int NT = kMfdNT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -101,50 +116,53 @@ __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* 
         S.z[i] = z;
         S.rb[i] = m;
     }
+    // ---- initial water of the region cells
+    for (int c = tid; c < NE; c += NT) {
+        const int ey = c / EX, ex = c - ey * EX;
+        const int64_t gx = ox + ex + 1, gy = oy + ey + 1;
+        float v = 0.0f;
+        if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny)
+            v = P.init ? rd_in(P.init, P, gy * P.nx + gx, 8) : 1.0f;
+        S.vhi[c] = v;
+        S.vlo[c] = 0.0f;
+    }
     __syncthreads();
 
-    // ---- per region cell: donors, bare / global flags, 1/S, initial water
+    // ---- per region cell: donors, bare / global flags, 1/S
     for (int c = tid; c < NE; c += NT) {
         const int ey = c / EX, ex = c - ey * EX;
         const int r = (ey + 1) * RX + ex + 1;
         const int64_t gx = ox + ex + 1, gy = oy + ey + 1;
         uint8_t dmr = 0, fin = 0x0F, b = 0;
-        float ih = 0.0f, il = 0.0f, vh = 0.0f;
+        float ih = 0.0f, il = 0.0f;
         if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
             uint32_t dmf = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 dmf |= (uint32_t)((S.rb[r + offy(k) * RX + offx(k)] >> opp(k)) & 1u) << k;
-            uint32_t in = 0xFFu;
-            if (ex == 0) in &= ~0x64u;       // W NW SW
-            if (ex == EX - 1) in &= ~0x91u;  // E NE SE
-            if (ey == 0) in &= ~0x32u;       // N NE NW
-            if (ey == EY - 1) in &= ~0xC8u;  // S SW SE
+            const uint32_t in = region_mask(ex, ey);
             dmr = (uint8_t)(dmf & in);
             b = (dmf & ~in) ? (uint8_t)kG : (uint8_t)0;
             fin = dmf == 0;
             const uint32_t m = S.rb[r] & grid_mask(gx, gy, P.nx, P.ny);
             if (m) {
+                // the eight weights are independent: evaluate them side by side
                 const float zc = S.z[r];
-                df s = df_make(0.0f);
-#pragma unroll 1
-                for (uint32_t mm = m; mm; mm &= mm - 1) {
-                    const int k = __ffs(mm) - 1;
-                    s = df_add(s, df_make(mfd_u_call(zc, S.z[r + offy(k) * RX + offx(k)], k, P.mc)));
-                }
-                const df inv = df_recip(s);
+                df t[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    t[k] = ((m >> k) & 1u) ? df_make(mfd_u(zc, S.z[r + offy(k) * RX + offx(k)], k, P.mc))
+                                           : df_make(0.0f);
+                const df inv = df_recip(df_tree8(t));
                 ih = inv.hi;
                 il = inv.lo;
             }
-            vh = P.init ? rd_in(P.init, P, gy * P.nx + gx, 8) : 1.0f;
         }
         S.dm[c] = dmr;
         S.fin[c] = fin;
         stb[c] = b;
         S.ihi[c] = ih;
         S.ilo[c] = il;
-        S.vhi[c] = vh;
-        S.vlo[c] = 0.0f;
     }
     __syncthreads();
 
@@ -165,60 +183,50 @@ __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* 
     }
     __syncthreads();
 
+    // Below, eight lanes serve one cell: lane k8 looks at direction k8.
+    const int k8 = tid & 7;
+    const int grp = tid >> 3;
+
     // ---- levels: finalise each level's list, collect the next one
     {
         int lo = 0, hi = S.qtail;
         while (lo < hi) {
-            for (int base = lo; base < hi; base += NT) {
-                const int i = base + tid;
-                int c = 0;
-                uint32_t ready = 0;  // codes of receivers whose count reached zero
-                if (i < hi) {
-                    c = S.queue[i];
-                    const bool glob = st_byte(S.st, c) & kG;
-                    const int ey = c / EX, ex = c - ey * EX;
-                    const int r = (ey + 1) * RX + ex + 1;
-                    const float zc = S.z[r];
+            for (int base = lo; base < hi; base += NG) {
+                const int i = base + grp;
+                const bool valid = i < hi;
+                const int c = valid ? (int)S.queue[i] : 0;
+                const bool glob = valid && (st_byte(S.st, c) & kG);
+                const int ey = c / EX, ex = c - ey * EX;
+                const int r = (ey + 1) * RX + ex + 1;
+                const bool inr = (region_mask(ex, ey) >> k8) & 1u;  // neighbour k8 inside the region
+                // pull: lane k8 takes the donor in direction k8
+                df term = df_make(0.0f);
+                if (valid && !glob && ((S.dm[c] >> k8) & 1u)) {
+                    const int j = c + offy(k8) * EX + offx(k8);
+                    const float u = mfd_u(S.z[r + offy(k8) * RX + offx(k8)], S.z[r], opp(k8), P.mc);
+                    term = df_mul(mfd_frac(u, df{S.ihi[j], S.ilo[j]}), df{S.vhi[j], S.vlo[j]});
+                }
+                const df total = df_tree8_lanes(term);
+                if (valid && k8 == 0) {
                     if (!glob) {
-                        df v = {S.vhi[c], S.vlo[c]};
-#pragma unroll 1
-                        for (uint32_t m = S.dm[c]; m; m &= m - 1) {
-                            const int k = __ffs(m) - 1;
-                            const int j = c + offy(k) * EX + offx(k);
-                            const float zj = S.z[r + offy(k) * RX + offx(k)];
-                            const df f = mfd_frac(mfd_u_call(zj, zc, opp(k), P.mc), df{S.ihi[j], S.ilo[j]});
-                            v = df_add(v, df_mul(f, df{S.vhi[j], S.vlo[j]}));
-                        }
+                        const df v = df_add(df{S.vhi[c], S.vlo[c]}, total);
                         S.vhi[c] = v.hi;
                         S.vlo[c] = v.lo;
                     }
                     S.fin[c] = 1;
-                    // receivers inside the region: pass on the global flag, count down
-                    uint32_t m = S.rb[r];
-                    if (ex == 0) m &= ~0x64u;
-                    if (ex == EX - 1) m &= ~0x91u;
-                    if (ey == 0) m &= ~0x32u;
-                    if (ey == EY - 1) m &= ~0xC8u;
-                    for (; m; m &= m - 1) {
-                        const int k = __ffs(m) - 1;
-                        const int t = c + offy(k) * EX + offx(k);
-                        if (S.fin[t] == 0x0F) continue;  // outside the grid
+                }
+                // receivers: lane k8 passes on the global flag and counts down
+                int ready = -1;
+                if (valid && inr && ((S.rb[r] >> k8) & 1u)) {
+                    const int t = c + offy(k8) * EX + offx(k8);
+                    if (S.fin[t] != 0x0F) {  // inside the grid
                         const uint32_t sh = 8u * (uint32_t)(t & 3);
                         if (glob) atomicOr(&S.st[t >> 2], kG << sh);
                         const uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
-                        if (((old >> sh) & 0x0Fu) == 1u) ready |= 1u << k;
+                        if (((old >> sh) & 0x0Fu) == 1u) ready = t;
                     }
                 }
-                // append the ready receivers, one warp-aggregated append per round
-                while (__any_sync(0xffffffffu, ready != 0)) {
-                    int cell = -1;
-                    if (ready) {
-                        const int k = __ffs(ready) - 1;
-                        ready &= ready - 1;
-                        cell = c + offy(k) * EX + offx(k);
-                    }
-                    push_cell(S, cell);
-                }
+                push_cell(S, ready);
             }
             __syncthreads();  // the level's values and the next list are complete
             lo = hi;
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* 
 
 }  // namespace
 
-// MFD forward accumulation: halo-tile local phase + walker phase.
+// MFD forward accumulation: halo-tile local phase + level-synchronous global phase.
 cudaError_t launch_mfd_forward(const Prob& P, EngineGlobals* G, cudaStream_t s) {
     constexpr size_t sm = sizeof(SmemMfd);
     cudaError_t e = cudaFuncSetAttribute(k_local_mfd, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -280,9 +288,7 @@ cudaError_t launch_mfd_forward(const Prob& P, EngineGlobals* G, cudaStream_t s) 
     k_local_mfd<<<(unsigned)tiles, kMfdNT, sm, s>>>(P, G);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_global<Mode::FwdMfd, true, false><<<walker_grid(), 256, 0, s>>>(
-        nullptr, P, G, (unsigned long long)(P.nx * P.ny));
-    return cudaGetLastError();
+    return launch_global<Mode::FwdMfd, true, false>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
 }
 
 }  // namespace fr
