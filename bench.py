@@ -383,7 +383,94 @@ def extra_rows(api, L, dev, peak):
                            "hbm_frac": (n * n * 8) / (ms * 1e-3) / 1e9 / peak}
     del zt, mask, w
     torch.cuda.empty_cache()
+    rows["batched"] = batch_rows(api, L, dev)
+    torch.cuda.empty_cache()
     return rows
+
+
+def batch_rows(api, L, dev):
+    """512 independent tiles (sides log-uniform in [64, 2048], beta in [1.8, 2.4],
+    rain U[0,1)): one fr_route_batch call replayed from a CUDA graph, against a
+    loop of per-tile fr_route_d8 / fr_route_mfd calls, for D8 and slope-split."""
+    import ctypes
+    import torch
+    from paper_2606_12800_gb300 import _lib, inputs
+    P = ctypes.c_void_p
+    specs = inputs.batch_specs(512, seed=SEED)
+    dems = [inputs.fractal_dem_torch(t.n_y, t.n_x, beta=t.beta, tilt=0.0, seed=t.seed, device="cuda")
+            for t in specs]
+    rains = [inputs.rain_field_torch(t.n_y, t.n_x, t.seed, device="cuda") for t in specs]
+    cells = sum(t.n_x * t.n_y for t in specs)
+    stream = torch.cuda.current_stream()
+    out = {"tiles": len(specs), "cells": cells,
+           "workload": "512 tiles, sides log-uniform in [64, 2048], beta U[1.8, 2.4], rain U[0,1), w out"}
+
+    def ev_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    for kind in ("d8", "mfd"):
+        k = _lib.FR_ROUTING_D8 if kind == "d8" else _lib.FR_ROUTING_MFD
+        route = [torch.empty((t.n_y, t.n_x), dtype=torch.uint8, device=dev) for t in specs]
+        w = [torch.empty((t.n_y, t.n_x), dtype=torch.float32, device=dev) for t in specs]
+        arr = (_lib.fr_tile * len(specs))()
+        for i, t in enumerate(specs):
+            a = arr[i]
+            a.dem, a.rain, a.w_out, a.w_lo_out, a.area_out = (dems[i].data_ptr(), rains[i].data_ptr(),
+                                                             w[i].data_ptr(), None, None)
+            a.route_out, a.nx, a.ny, a.dx = route[i].data_ptr(), t.n_x, t.n_y, DX
+        tiles_dev = torch.frombuffer(bytearray(bytes(memoryview(arr).cast("B"))),
+                                     dtype=torch.uint8).to(dev)
+        need = int(L.fr_batch_workspace_size(arr, len(specs), k, 0))
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        wsp = P(ws.data_ptr())
+
+        def batched():
+            _lib.check(L.fr_route_batch(arr, P(tiles_dev.data_ptr()), len(specs), k, 1.1, 0, wsp, need,
+                                        api._stream()), "fr_route_batch")
+        _lib.check(L.fr_batch_autotune(arr, P(tiles_dev.data_ptr()), len(specs), k, 1.1, 0, wsp, need,
+                                       api._stream()), "fr_batch_autotune")
+        torch.cuda.synchronize()
+        row = {}
+        row["batched_ms"] = ev_time(batched, 5)
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                batched()
+            row["batched_graph_ms"] = ev_time(g.replay, 5)
+            del g
+        except Exception as e:  # pragma: no cover
+            row["batched_graph_ms"] = None
+            row["graph_error"] = str(e)[:200]
+        st = int(L.fr_get_status(wsp, need, api._stream()))
+        row["status"] = st
+        tws = api.workspace(2048, 2048, dev)
+        twsp, twsn = P(tws.data_ptr()), tws.numel()
+
+        def per_tile():
+            s = api._stream()
+            for i, t in enumerate(specs):
+                if kind == "d8":
+                    L.fr_route_d8(P(dems[i].data_ptr()), t.n_x, t.n_y, DX, 0, P(rains[i].data_ptr()),
+                                  P(w[i].data_ptr()), None, None, P(route[i].data_ptr()), twsp, twsn, s)
+                else:
+                    L.fr_route_mfd(P(dems[i].data_ptr()), t.n_x, t.n_y, DX, 1.1, 0, P(rains[i].data_ptr()),
+                                   P(w[i].data_ptr()), None, P(route[i].data_ptr()), twsp, twsn, s)
+        row["per_tile_ms"] = ev_time(per_tile, 3)
+        best = row["batched_graph_ms"] or row["batched_ms"]
+        row["cells_per_s"] = cells / (best * 1e-3)
+        row["per_tile_cells_per_s"] = cells / (row["per_tile_ms"] * 1e-3)
+        row["speedup_vs_per_tile"] = row["per_tile_ms"] / best
+        out[kind] = row
+        del route, w, ws, tiles_dev
+    return out
 
 
 if __name__ == "__main__":

@@ -24,11 +24,7 @@ struct BatchLayout {
 
 __host__ __device__ inline int64_t cnt_bytes(int64_t n) { return (n + 4 + 3) & ~(int64_t)3; }
 __host__ __device__ inline int64_t gbit_words(int64_t n) { return (n + 31) / 32; }
-__host__ __device__ inline int64_t eng_tiles(int64_t nx, int64_t ny) {
-    return ((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY);
-}
-
-BatchLayout batch_layout(const fr_tile* t, int n) {
+BatchLayout batch_layout(const fr_tile* t, int n, int kind = FR_ROUTING_D8, int geo = 0) {
     BatchLayout L{};
     int64_t cb = 0, gw = 0, cells = 0, et = 0;
     for (int i = 0; i < n; ++i) {
@@ -36,7 +32,7 @@ BatchLayout batch_layout(const fr_tile* t, int n) {
         cb += cnt_bytes(c);
         gw += gbit_words(c);
         cells += c;
-        et += eng_tiles(t[i].nx, t[i].ny);
+        et += halo_tiles(kind == FR_ROUTING_MFD, geo, t[i].nx, t[i].ny);
     }
     size_t off = 256;
     L.cnt = off;
@@ -67,7 +63,7 @@ BatchLayout batch_layout(const fr_tile* t, int n) {
 constexpr int SETUP_NT = 1024;
 
 __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restrict__ tiles, int n,
-                                                          int kind, double p, char* ws,
+                                                          int kind, int geo, double p, char* ws,
                                                           BatchLayout L, EngineGlobals* G) {
     __shared__ int64_t sh[4][SETUP_NT];
     const int tid = threadIdx.x;
@@ -80,7 +76,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restr
         s_gw += gbit_words(c);
         s_cells += c;
         s_rt += receiver_tiles(tiles[i].nx, tiles[i].ny);
-        s_et += eng_tiles(tiles[i].nx, tiles[i].ny);
+        s_et += halo_tiles(kind == FR_ROUTING_MFD, geo, tiles[i].nx, tiles[i].ny);
     }
     // exclusive scan of the per-thread sums (cb, gw, cells, recv tiles); engine
     // tiles share the cell scan's slot below
@@ -144,7 +140,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restr
         o_gw += gbit_words(c);
         o_cells += c;
         o_rt += receiver_tiles(t.nx, t.ny);
-        o_et += eng_tiles(t.nx, t.ny);
+        o_et += halo_tiles(kind == FR_ROUTING_MFD, geo, t.nx, t.ny);
     }
     if (e == n && b < e) {  // the thread holding the last tile writes the totals
         pre_recv[n] = o_rt;
@@ -172,9 +168,11 @@ bool tiles_ok(const fr_tile* t, int n, int kind) {
     return true;
 }
 
-// Persistent grid multipliers (CTAs per SM) for the receiver and engine stages.
+// Tuned launch shape of the batched route: CTAs per SM of the persistent
+// receiver stage, and the halo-tile geometry of the D8 local stage
+// (0: 128x32 inner tiles, 1: 64x32).
 struct Tune {
-    int recv = 8, eng = 4;
+    int recv = 8, geo = 0;
 };
 Tune g_tune[2];
 std::mutex g_tune_mutex;
@@ -192,20 +190,23 @@ int sm_count() {
 
 cudaError_t run_batch(const fr_tile* th, const fr_tile* td, int n, int kind, double p, uint32_t flags,
                       char* ws, const Tune& tune, cudaStream_t s) {
-    const BatchLayout L = batch_layout(th, n);
+    const int geo = kind == FR_ROUTING_D8 ? tune.geo : 0;
+    const BatchLayout L = batch_layout(th, n, kind, geo);
     EngineGlobals* G = reinterpret_cast<EngineGlobals*>(ws);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, s);
     if (e != cudaSuccess) return e;
-    k_batch_setup<<<1, SETUP_NT, 0, s>>>(td, n, kind, p, ws, L, G);
+    k_batch_setup<<<1, SETUP_NT, 0, s>>>(td, n, kind, geo, p, ws, L, G);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const Prob* probs = reinterpret_cast<const Prob*>(ws + L.probs);
     e = launch_receivers_batch(kind, probs, reinterpret_cast<const int64_t*>(ws + L.pre_recv), n,
                                flags, G, sm_count() * tune.recv, s);
     if (e != cudaSuccess) return e;
     const bool w = th[0].w_out != nullptr, a = th[0].area_out != nullptr;
-    return launch_engine_batch(kind == FR_ROUTING_D8 ? Mode::FwdD8 : Mode::FwdMfd, w, a, probs,
-                               reinterpret_cast<const int64_t*>(ws + L.pre_eng), n, L.eng_tiles,
-                               (unsigned long long)L.cells, G, sm_count() * tune.eng, s);
+    const int64_t* pre = reinterpret_cast<const int64_t*>(ws + L.pre_eng);
+    if (kind == FR_ROUTING_D8)
+        return launch_d8_forward_batch(geo, w, a, probs, pre, n, L.eng_tiles,
+                                       (unsigned long long)L.cells, G, s);
+    return launch_mfd_forward_batch(probs, pre, n, L.eng_tiles, (unsigned long long)L.cells, G, s);
 }
 
 }  // namespace
@@ -251,14 +252,14 @@ fr_status fr_batch_autotune(const fr_tile* tiles_host, const fr_tile* tiles_dev,
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return FR_ERR_CUDA;
     const int recv_opts[] = {2, 4, 8, 16};
-    const int eng_opts[] = {1, 2, 3, 4, 6};
+    const int geos = kind == FR_ROUTING_D8 ? kD8Geometries : 1;
     Tune best;
     float best_ms = 1e30f;
     for (int r : recv_opts) {
-        for (int en : eng_opts) {
+        for (int geo = 0; geo < geos; ++geo) {
             Tune t;
             t.recv = r;
-            t.eng = en;
+            t.geo = geo;
             float ms_sum = 0.f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(a, s);

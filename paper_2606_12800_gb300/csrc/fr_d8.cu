@@ -120,10 +120,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Marks one global inner cell (rare): its bit and a list entry.
-__device__ __forceinline__ void mark_one(const Prob& P, EngineGlobals* G, int64_t gi) {
+__device__ __forceinline__ void mark_one(const Prob& P, EngineGlobals* G, int64_t gi, int pid) {
     atomicOr(P.gbits + (gi >> 5), 1u << (gi & 31));
     const unsigned long long slot = atomicAdd(&G->glist_count, 1ull);
-    if (FR_OK((int64_t)slot, P.glist_cap, 17)) P.glist[slot] = (unsigned long long)gi;
+    if (FR_OK((int64_t)slot, P.glist_cap, 17))
+        P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
 }
 
 // Warp-aggregated append of up to four cells per lane (all lanes call).
@@ -144,16 +145,36 @@ __device__ __forceinline__ void push_starts(S_& S, int n, const int (&cells)[4])
     for (int q = 0; q < n; ++q) S.queue[base + q] = (uint16_t)cells[q];
 }
 
-template <class Gm, bool W, bool AREA>
-__global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
+// Problem and tile of this CTA: one problem, or (batched) the problem whose
+// tiles [prefix[p], prefix[p+1]) hold blockIdx.x.
+__device__ __forceinline__ int batch_problem(const int64_t* __restrict__ prefix, int nprob,
+                                             int64_t& lt) {
+    int lo = 0, hi = nprob - 1;
+    const int64_t b = (int64_t)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    lt = b - prefix[lo];
+    return lo;
+}
+
+template <class Gm, bool W, bool AREA, bool BATCH>
+__global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
+                                                  const Prob* __restrict__ probs,
+                                                  const int64_t* __restrict__ prefix, int nprob) {
     constexpr int TX = Gm::TX, TY = Gm::TY, H = Gm::H, EX = Gm::EX, EY = Gm::EY, NE = Gm::NE;
     constexpr int RY = Gm::RY, CP = Gm::CP;
     using Sm = SmemD8<Gm, W, AREA>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm& S = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
+    int64_t lt = (int64_t)blockIdx.x;
+    const int pid = BATCH ? batch_problem(prefix, nprob, lt) : 0;
+    const Prob& P = BATCH ? probs[pid] : Pone;
     const int64_t tiles_x = (P.nx + TX - 1) / TX;
-    const int64_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    const int64_t ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int64_t x0 = tx * TX, y0 = ty * TY;
     // ring origin (may be negative) and the grid's extent in ring coordinates
     const int64_t ox = x0 - H - 1, oy = y0 - H - 1;
@@ -412,7 +433,7 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
         const int c = (ly + H) * EX + lx + H;
         const int64_t gi = gy * P.nx + gx;
         if (stget(S.st, c) & kG) {
-            mark_one(P, G, gi);
+            mark_one(P, G, gi, pid);
             return;
         }
         if (S.fin[c] != 1) return;  // never reached (a cycle)
@@ -463,22 +484,45 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob P, EngineGlobals* G) {
     if (tid == 0 && S.done) atomicAdd(&G->done_cells, S.done);
 }
 
-template <class Gm, bool W, bool AREA>
-cudaError_t launch_d8(const Prob& P, EngineGlobals* G, cudaStream_t s) {
+template <class Gm, bool W, bool AREA, bool BATCH>
+cudaError_t launch_local_d8(const Prob& P, EngineGlobals* G, const Prob* probs,
+                            const int64_t* prefix, int nprob, int64_t tiles, cudaStream_t s) {
     constexpr size_t sm = sizeof(SmemD8<Gm, W, AREA>);
-    cudaError_t e = cudaFuncSetAttribute(k_local_d8<Gm, W, AREA>,
+    cudaError_t e = cudaFuncSetAttribute(k_local_d8<Gm, W, AREA, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = ((P.nx + Gm::TX - 1) / Gm::TX) * ((P.ny + Gm::TY - 1) / Gm::TY);
-    k_local_d8<Gm, W, AREA><<<(unsigned)tiles, NT8, sm, s>>>(P, G);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_global<Mode::FwdD8, W, AREA><<<walker_grid(), 256, 0, s>>>(nullptr, P, G,
-                                                                 (unsigned long long)(P.nx * P.ny));
+    if (tiles > 0) k_local_d8<Gm, W, AREA, BATCH><<<(unsigned)tiles, NT8, sm, s>>>(P, G, probs, prefix, nprob);
     return cudaGetLastError();
 }
 
-using GeoD8 = D8Geo<128, 32>;
+template <class Gm, bool W, bool AREA>
+cudaError_t launch_d8(const Prob& P, EngineGlobals* G, cudaStream_t s) {
+    const int64_t tiles = ((P.nx + Gm::TX - 1) / Gm::TX) * ((P.ny + Gm::TY - 1) / Gm::TY);
+    cudaError_t e = launch_local_d8<Gm, W, AREA, false>(P, G, nullptr, nullptr, 1, tiles, s);
+    if (e != cudaSuccess) return e;
+    return launch_global<Mode::FwdD8, W, AREA>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
+}
+
+template <class Gm, bool W, bool AREA>
+cudaError_t launch_d8_batch(const Prob* probs, const int64_t* prefix, int nprob, int64_t tiles,
+                            unsigned long long total_cells, EngineGlobals* G, cudaStream_t s) {
+    Prob none{};
+    cudaError_t e = launch_local_d8<Gm, W, AREA, true>(none, G, probs, prefix, nprob, tiles, s);
+    if (e != cudaSuccess) return e;
+    return launch_global<Mode::FwdD8, W, AREA>(probs, none, G, total_cells, s);
+}
+
+using GeoD8 = D8Geo<kD8TileX, kD8TileY>;        // geometry 0
+using GeoD8s = D8Geo<kD8TileX / 2, kD8TileY>;   // geometry 1: narrower tiles, 3 CTAs per SM
+
+template <class Gm>
+cudaError_t d8_batch_w(bool want_w, bool want_area, const Prob* probs, const int64_t* prefix,
+                       int nprob, int64_t tiles, unsigned long long cells, EngineGlobals* G,
+                       cudaStream_t s) {
+    if (want_w && want_area) return launch_d8_batch<Gm, true, true>(probs, prefix, nprob, tiles, cells, G, s);
+    if (want_w) return launch_d8_batch<Gm, true, false>(probs, prefix, nprob, tiles, cells, G, s);
+    return launch_d8_batch<Gm, false, true>(probs, prefix, nprob, tiles, cells, G, s);
+}
 
 }  // namespace
 
@@ -488,6 +532,15 @@ cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& P, Engine
     if (want_w && want_area) return launch_d8<GeoD8, true, true>(P, G, s);
     if (want_w) return launch_d8<GeoD8, true, false>(P, G, s);
     return launch_d8<GeoD8, false, true>(P, G, s);
+}
+
+// Batched D8 forward: the CTAs of all problems' tiles in one launch (tile
+// prefix of the chosen geometry), then one walker phase.
+cudaError_t launch_d8_forward_batch(int geo, bool want_w, bool want_area, const Prob* probs,
+                                    const int64_t* prefix, int nprob, int64_t tiles,
+                                    unsigned long long total_cells, EngineGlobals* G, cudaStream_t s) {
+    if (geo == 1) return d8_batch_w<GeoD8s>(want_w, want_area, probs, prefix, nprob, tiles, total_cells, G, s);
+    return d8_batch_w<GeoD8>(want_w, want_area, probs, prefix, nprob, tiles, total_cells, G, s);
 }
 
 }  // namespace fr

@@ -929,7 +929,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // Barrier over all blocks of a cooperative launch.  Returns false (and leaves
 // FR_ERR_NO_PROGRESS in the status word) if the wait exceeds the time limit.
-static __device__ __noinline__ bool grid_barrier(EngineGlobals* G) {
+static __device__ __noinline__ bool grid_barrier(EngineGlobals* G, unsigned nblocks) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -937,7 +937,7 @@ static __device__ __noinline__ bool grid_barrier(EngineGlobals* G) {
         const unsigned gen = ld_acquire_u32(&G->bar_gen);
         __threadfence();
         const unsigned arrived = atomicAdd(&G->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == nblocks - 1) {
             atomicExch(&G->bar_count, 0u);
             __threadfence();
             atomicAdd(&G->bar_gen, 1u);
@@ -997,13 +997,18 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
     unsigned long long* const buf_b = P0.glist;
     const unsigned long long cap = (unsigned long long)P0.glist_cap;
     const unsigned long long count = __ldcg(&G->glist_count);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // only as many blocks as the global cells need take part (every block
+    // computes the same number), so a small problem's barriers stay cheap
+    const unsigned long long want = (count + blockDim.x - 1) / blockDim.x;
+    const unsigned nb = (unsigned)(want < gridDim.x ? want : gridDim.x);
+    const unsigned long long stride = (unsigned long long)nb * blockDim.x;
     const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     constexpr unsigned long long kCellMask = (1ull << 40) - 1;
     unsigned long long done = 0;
+    bool ok = blockIdx.x < nb;
     // first frontier: global cells without global dependencies; the others'
     // counters start at kReadyAt - dependencies
-    for (unsigned long long i = first; i < count; i += stride) {
+    if (ok) for (unsigned long long i = first; i < count; i += stride) {
         const unsigned long long item = __ldcg(buf_b + i);
         const Prob& P = probs ? probs[(int)(item >> 40)] : single;
         const int64_t cell = (int64_t)(item & kCellMask);
@@ -1015,7 +1020,7 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
         const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
         if (FR_OK((int64_t)slot, (int64_t)cap, 18)) buf_a[slot] = item;
     }
-    bool ok = grid_barrier(G);
+    if (ok) ok = grid_barrier(G, nb);
     for (int round = 1; ok; ++round) {
         unsigned long long* cur = (round & 1) ? buf_a : buf_b;
         unsigned long long* nxt = (round & 1) ? buf_b : buf_a;
@@ -1033,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
             step_round<E>(P, (int64_t)(item & kCellMask), item & ~kCellMask, nxt, ncount, cap);
             ++done;
         }
-        ok = grid_barrier(G);
+        ok = grid_barrier(G, nb);
     }
     for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
     if (threadIdx.x == 0) s_done = 0;

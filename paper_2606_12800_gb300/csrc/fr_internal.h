@@ -73,10 +73,20 @@ cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Pr
                                 EngineGlobals* g, int grid, cudaStream_t s);
 int walker_grid();
 // D8 forward: halo-tile local phase (fr_d8.cu) + walker phase.
-// MFD forward accumulation: halo-tile local phase + walker phase (fr_mfd.cu).
-cudaError_t launch_mfd_forward(const Prob& prob, EngineGlobals* g, cudaStream_t s);
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
                               cudaStream_t s);
+// MFD forward: halo-tile local phase (fr_mfd.cu) + level-synchronous global phase.
+cudaError_t launch_mfd_forward(const Prob& prob, EngineGlobals* g, cudaStream_t s);
+// Batched forms: one CTA per tile of every problem (tile_prefix over the
+// halo geometry geo, see halo_tiles), then one global phase.
+cudaError_t launch_d8_forward_batch(int geo, bool want_w, bool want_area, const Prob* probs_dev,
+                                    const int64_t* tile_prefix_dev, int nprob, int64_t total_tiles,
+                                    unsigned long long total_cells, EngineGlobals* g,
+                                    cudaStream_t s);
+cudaError_t launch_mfd_forward_batch(const Prob* probs_dev, const int64_t* tile_prefix_dev,
+                                     int nprob, int64_t total_tiles,
+                                     unsigned long long total_cells, EngineGlobals* g,
+                                     cudaStream_t s);
 cudaError_t launch_mfd_grad_z(const Prob& prob, const float* g_hi, const float* g_lo,
                               float* dLdz, cudaStream_t s);
 cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t* rb,
@@ -93,9 +103,21 @@ __host__ __device__ inline int64_t receiver_tiles(int64_t nx, int64_t ny) {
     return ((nx + kRecvTileX - 1) / kRecvTileX) * ((ny + kRecvTileY - 1) / kRecvTileY);
 }
 
-// Engine tile shape (cells): every launch uses the same tile so that the
-// batched and single-grid paths share counters and queues.
+// Engine tile shape (cells) of the generic tile kernel (adjoints).
 constexpr int kTileX = 64;
 constexpr int kTileY = 32;
+
+// Inner tiles of the halo kernels: D8 geometry 0 is kD8TileX x kD8TileY,
+// geometry 1 half as wide; MFD uses kMfdTileX x kMfdTileY.
+constexpr int kD8TileX = 128;
+constexpr int kD8TileY = 32;
+constexpr int kMfdTileX = 64;
+constexpr int kMfdTileY = 32;
+constexpr int kD8Geometries = 2;
+__host__ __device__ inline int64_t halo_tiles(int kind_mfd, int geo, int64_t nx, int64_t ny) {
+    const int64_t tx = kind_mfd ? kMfdTileX : (geo == 1 ? kD8TileX / 2 : kD8TileX);
+    const int64_t ty = kind_mfd ? kMfdTileY : kD8TileY;
+    return ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+}
 
 }  // namespace fr

@@ -26,7 +26,7 @@
 namespace fr {
 namespace {
 
-constexpr int kMfdTX = 64, kMfdTY = 32, kMfdH = 8;
+constexpr int kMfdTX = kMfdTileX, kMfdTY = kMfdTileY, kMfdH = 8;
 constexpr int kMfdNT = 512;
 constexpr int NG = kMfdNT / 8;  // cells served at once (eight lanes each)
 
@@ -70,10 +70,12 @@ __device__ __forceinline__ uint32_t st_byte(const uint32_t* st, int c) {
 }
 
 // Marks one global inner cell: its bit and a list entry.
-__device__ __forceinline__ void mark_global_cell(const Prob& P, EngineGlobals* G, int64_t gi) {
+__device__ __forceinline__ void mark_global_cell(const Prob& P, EngineGlobals* G, int64_t gi,
+                                                 int pid) {
     atomicOr(P.gbits + (gi >> 5), 1u << (gi & 31));
     const unsigned long long slot = atomicAdd(&G->glist_count, 1ull);
-    if (FR_OK((int64_t)slot, P.glist_cap, 17)) P.glist[slot] = (unsigned long long)gi;
+    if (FR_OK((int64_t)slot, P.glist_cap, 17))
+        P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
 }
 
 // Warp-aggregated append of one optional cell per lane (all lanes call).
@@ -87,7 +89,26 @@ __device__ __forceinline__ void push_cell(SmemMfd& S, int cell) {
     if (cell >= 0) S.queue[b0 + __popc(pm & ((1u << lane) - 1u))] = (uint16_t)cell;
 }
 
-__global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* G) {
+// Problem and tile of this CTA in a batched launch: the problem whose tiles
+// [prefix[p], prefix[p+1]) hold blockIdx.x.
+__device__ __forceinline__ int batch_problem_mfd(const int64_t* __restrict__ prefix, int nprob,
+                                                 int64_t& lt) {
+    int lo = 0, hi = nprob - 1;
+    const int64_t b = (int64_t)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    lt = b - prefix[lo];
+    return lo;
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob Pone, EngineGlobals* G,
+                                                         const Prob* __restrict__ probs,
+                                                         const int64_t* __restrict__ prefix,
+                                                         int nprob) {
     constexpr int TX = MfdGeo::TX, TY = MfdGeo::TY, H = MfdGeo::H;
     constexpr int EX = MfdGeo::EX, NE = MfdGeo::NE;
     constexpr int RX = MfdGeo::RX, NR = MfdGeo::NR;
@@ -96,8 +117,11 @@ __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* 
     SmemMfd& S = *reinterpret_cast<SmemMfd*>(smem_raw);
     uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
     const int tid = threadIdx.x;
+    int64_t lt = (int64_t)blockIdx.x;
+    const int pid = BATCH ? batch_problem_mfd(prefix, nprob, lt) : 0;
+    const Prob& P = BATCH ? probs[pid] : Pone;
     const int64_t tiles_x = (P.nx + TX - 1) / TX;
-    const int64_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    const int64_t ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int64_t x0 = tx * TX, y0 = ty * TY;
     const int64_t ox = x0 - H - 1, oy = y0 - H - 1;  // ring origin (may be negative)
     if (tid == 0) S.qtail = 0;
@@ -244,7 +268,7 @@ __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* 
         const int c = (ly + H) * EX + lx + H;
         const int64_t gi = gy * P.nx + gx;
         if (st_byte(S.st, c) & kG) {
-            mark_global_cell(P, G, gi);
+            mark_global_cell(P, G, gi, pid);
             continue;
         }
         if (S.fin[c] != 1) continue;  // never reached (a cycle in a caller's masks)
@@ -276,19 +300,36 @@ __global__ void __launch_bounds__(kMfdNT, 2) k_local_mfd(Prob P, EngineGlobals* 
     if (tid == 0 && S.done) atomicAdd(&G->done_cells, S.done);
 }
 
+template <bool BATCH>
+cudaError_t launch_local_mfd(const Prob& P, EngineGlobals* G, const Prob* probs,
+                             const int64_t* prefix, int nprob, int64_t tiles, cudaStream_t s) {
+    constexpr size_t sm = sizeof(SmemMfd);
+    cudaError_t e = cudaFuncSetAttribute(k_local_mfd<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    if (tiles > 0) k_local_mfd<BATCH><<<(unsigned)tiles, kMfdNT, sm, s>>>(P, G, probs, prefix, nprob);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // MFD forward accumulation: halo-tile local phase + level-synchronous global phase.
 cudaError_t launch_mfd_forward(const Prob& P, EngineGlobals* G, cudaStream_t s) {
-    constexpr size_t sm = sizeof(SmemMfd);
-    cudaError_t e = cudaFuncSetAttribute(k_local_mfd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
     const int64_t tiles = ((P.nx + kMfdTX - 1) / kMfdTX) * ((P.ny + kMfdTY - 1) / kMfdTY);
-    k_local_mfd<<<(unsigned)tiles, kMfdNT, sm, s>>>(P, G);
-    e = cudaGetLastError();
+    cudaError_t e = launch_local_mfd<false>(P, G, nullptr, nullptr, 1, tiles, s);
     if (e != cudaSuccess) return e;
     return launch_global<Mode::FwdMfd, true, false>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
+}
+
+// Batched MFD forward: the CTAs of all problems' tiles in one launch, then one
+// global phase.
+cudaError_t launch_mfd_forward_batch(const Prob* probs, const int64_t* prefix, int nprob,
+                                     int64_t tiles, unsigned long long total_cells,
+                                     EngineGlobals* G, cudaStream_t s) {
+    Prob none{};
+    cudaError_t e = launch_local_mfd<true>(none, G, probs, prefix, nprob, tiles, s);
+    if (e != cudaSuccess) return e;
+    return launch_global<Mode::FwdMfd, true, false>(probs, none, G, total_cells, s);
 }
 
 }  // namespace fr
