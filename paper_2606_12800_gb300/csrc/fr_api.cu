@@ -264,8 +264,7 @@ fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_l
     P.lo_full = dLdz_out ? 1 : 0;  // the elevation gradient reads every trailing word
     const Layout L = layout(n);
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return FR_ERR_CUDA;
-    const Mode m = R->kind == FR_ROUTING_D8 ? Mode::AdjD8 : Mode::AdjMfd;
-    cudaError_t e = launch_engine(m, true, false, P, reinterpret_cast<EngineGlobals*>(ws), s);
+    cudaError_t e = launch_adjoint(R->kind == FR_ROUTING_MFD, P, reinterpret_cast<EngineGlobals*>(ws), s);
     if (e != cudaSuccess) return FR_ERR_CUDA;
     if (dLdz_out) {
         e = launch_mfd_grad_z(P, dLdr_out, P.out_lo, dLdz_out, s);

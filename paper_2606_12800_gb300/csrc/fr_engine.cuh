@@ -212,14 +212,18 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
                 inv = g_inv_norm<E>(P, t);
                 zc = rd_z(P, t);
             }
-#pragma unroll 1
+            // receiver terms in the fixed pairwise order of df_tree8
+            df term[8];
+#pragma unroll
             for (int k = 0; k < 8; ++k) {
+                term[k] = df_make(0.0f);
                 if (!((recv >> k) & 1u)) continue;
-                int64_t j = t + offi(k, P.nx);
-                df gj = g_value<E>(P, j);
-                if constexpr (E::kMfd) gj = df_mul(mfd_frac(mfd_u_call(zc, rd_z(P, j), k, P.mc), inv), gj);
-                v = df_add(v, gj);
+                const int64_t j = t + offi(k, P.nx);
+                const df gj = g_value<E>(P, j);
+                if constexpr (E::kMfd) term[k] = df_mul(mfd_frac(mfd_u_call(zc, rd_z(P, j), k, P.mc), inv), gj);
+                else term[k] = gj;
             }
+            v = df_add(v, df_tree8(term));
         } else {
             float zc = E::kMfd ? rd_z(P, t) : 0.0f;
             // routing bytes of the eight neighbours, loaded side by side

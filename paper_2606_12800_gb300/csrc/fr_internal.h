@@ -75,8 +75,10 @@ int walker_grid();
 // D8 forward: halo-tile local phase (fr_d8.cu) + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
                               cudaStream_t s);
-// MFD forward: halo-tile local phase (fr_mfd.cu) + level-synchronous global phase.
+// MFD forward: halo-tile local phase (fr_halo.cu) + level-synchronous global phase.
 cudaError_t launch_mfd_forward(const Prob& prob, EngineGlobals* g, cudaStream_t s);
+// Adjoint of D8 or MFD routing: halo-tile local phase (fr_halo.cu) + global phase.
+cudaError_t launch_adjoint(bool mfd, const Prob& prob, EngineGlobals* g, cudaStream_t s);
 // Batched forms: one CTA per tile of every problem (tile_prefix over the
 // halo geometry geo, see halo_tiles), then one global phase.
 cudaError_t launch_d8_forward_batch(int geo, bool want_w, bool want_area, const Prob* probs_dev,
