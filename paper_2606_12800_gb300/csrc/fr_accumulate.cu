@@ -1,38 +1,9 @@
-// fr_accumulate.cu -- launches of the tile engine, the mass-balance reduction
-// and the MFD elevation-gradient stencil.
+// fr_accumulate.cu -- the D8 walker grid, the mass-balance reduction and the
+// MFD elevation-gradient stencil.
 #include "fr_engine.cuh"
 
 namespace fr {
 namespace {
-
-template <Mode M, bool W, bool A>
-cudaError_t launch_single(const Prob& P, EngineGlobals* G, cudaStream_t s) {
-    constexpr size_t sm = engine_smem<M, W, A>();
-    cudaError_t e = cudaFuncSetAttribute(k_local<M, W, A>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    const int64_t tiles_y = (P.ny + kTileY - 1) / kTileY;
-    const int64_t tiles = tiles_y * P.tiles_x;
-    k_local<M, W, A><<<(unsigned)tiles, 256, sm, s>>>(P, G);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_global<M, W, A>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
-}
-
-template <Mode M, bool W, bool A>
-cudaError_t launch_batch(const Prob* probs, const int64_t* prefix, int nprob, int64_t total_tiles,
-                         unsigned long long total_cells, EngineGlobals* G, int grid,
-                         cudaStream_t s) {
-    constexpr size_t sm = engine_smem<M, W, A>();
-    cudaError_t e = cudaFuncSetAttribute(k_local_batch<M, W, A>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_local_batch<M, W, A><<<grid, 256, sm, s>>>(probs, prefix, nprob, total_tiles, G);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    Prob none{};
-    return launch_global<M, W, A>(probs, none, G, total_cells, s);
-}
 
 // ---------------------------------------------------------------- mass balance
 constexpr int MB_NT = 256;
@@ -234,45 +205,6 @@ int walker_grid() {
         grid = (sms > 0 ? sms : 152) * 8;
     }
     return grid;
-}
-
-cudaError_t launch_engine(Mode mode, bool want_w, bool want_area, const Prob& P,
-                          EngineGlobals* G, cudaStream_t s) {
-    switch (mode) {
-        case Mode::FwdD8:
-            if (want_w && want_area) return launch_single<Mode::FwdD8, true, true>(P, G, s);
-            if (want_w) return launch_single<Mode::FwdD8, true, false>(P, G, s);
-            return launch_single<Mode::FwdD8, false, true>(P, G, s);
-        case Mode::FwdMfd:
-            return launch_single<Mode::FwdMfd, true, false>(P, G, s);
-        case Mode::AdjD8:
-            return launch_single<Mode::AdjD8, true, false>(P, G, s);
-        case Mode::AdjMfd:
-            return launch_single<Mode::AdjMfd, true, false>(P, G, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Prob* probs,
-                                const int64_t* prefix, int32_t nprob, int64_t total_tiles,
-                                unsigned long long total_cells, EngineGlobals* G, int grid,
-                                cudaStream_t s) {
-    switch (mode) {
-        case Mode::FwdD8:
-            if (want_w && want_area)
-                return launch_batch<Mode::FwdD8, true, true>(probs, prefix, nprob, total_tiles,
-                                                             total_cells, G, grid, s);
-            if (want_w)
-                return launch_batch<Mode::FwdD8, true, false>(probs, prefix, nprob, total_tiles,
-                                                              total_cells, G, grid, s);
-            return launch_batch<Mode::FwdD8, false, true>(probs, prefix, nprob, total_tiles,
-                                                          total_cells, G, grid, s);
-        case Mode::FwdMfd:
-            return launch_batch<Mode::FwdMfd, true, false>(probs, prefix, nprob, total_tiles,
-                                                           total_cells, G, grid, s);
-        default:
-            return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_mfd_grad_z(const Prob& P, const float* g_hi, const float* g_lo, float* dLdz,

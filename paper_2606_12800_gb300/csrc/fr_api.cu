@@ -18,7 +18,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Workspace layout (same for every operation on an nx*ny grid):
 //   globals (64 B) | arrival counters (1 B/cell) | global-cell bits (1 bit/cell)
-//   | trailing words (4 B/cell) | walker links (8 B/cell)
+//   | trailing words (4 B/cell) | frontier buffer (8 B/cell)
 //   | global-cell list (8 B/cell) | routing bytes (1 B/cell) | mass partials
 // The first three regions are zeroed by each engine call (one memset).
 struct Layout {
@@ -101,7 +101,6 @@ Prob base_prob(const fr_routing* R, char* ws) {
     P.glist_cap = R->nx * R->ny;
     P.out_lo = reinterpret_cast<float*>(ws + L.lo);
     P.mc = make_mfd_const(R->kind == FR_ROUTING_MFD ? R->dx : 1.0, R->kind == FR_ROUTING_MFD ? R->p : 1.0);
-    P.tiles_x = (int32_t)((R->nx + kTileX - 1) / kTileX);
     return P;
 }
 

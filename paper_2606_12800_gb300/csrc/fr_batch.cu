@@ -131,8 +131,6 @@ __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restr
         P.glist = reinterpret_cast<unsigned long long*>(ws + L.glist);
         P.glist_cap = L.cells;
         P.mc = make_mfd_const(t.dx, kind == FR_ROUTING_MFD ? p : 1.0);
-        P.tiles_x = (int32_t)((t.nx + kTileX - 1) / kTileX);
-        P.tile_base = o_et;
         probs[i] = P;
         pre_recv[i] = o_rt;
         pre_eng[i] = o_et;

@@ -1,32 +1,32 @@
-// fr_engine.cuh -- exact accumulation over a routing DAG on a DEM grid.
+// fr_engine.cuh -- shared pieces of exact accumulation over a routing DAG.
 //
-// Global flow routing solves A w = r with A = I - W (paper Sec. 2.2); the
-// adjoint solves A^T g = gbar.  Both are triangular once cells are processed
-// in dependency order (Sec. 2.4), which is what the sequential high-to-low
+// Global flow routing solves A w = r with A = I - W (Sec. 2.2); the adjoint
+// solves A^T g = gbar.  Both are triangular once cells are processed in
+// dependency order (Sec. 2.4), which is what the sequential high-to-low
 // algorithm does (Sec. 2.1).  On the GPU the grid is cut into CTA tiles that
-// play the role of the paper's per-process subdomains (Sec. 2.4, "each
-// process can solve its linear system independently"):
+// play the role of the paper's per-process subdomains (Sec. 2.4), extended by
+// a halo so that the subdomains overlap:
 //
-//  1. local phase (shared memory): every tile cell whose dependencies all lie
-//     inside the tile -- and recursively inside -- is solved exactly by a
-//     level-synchronous wavefront over the tile's DAG (a topological order;
-//     Sec. 3.2 shows any such order gives the same result).  The frontier is a
-//     shared-memory queue appended with warp-aggregated atomics.  Cells with a
-//     dependency outside the tile (and everything they feed inside it) are
-//     marked "global".
-//  2. global phase (a second kernel, after every tile is done): instead of
-//     the paper's Richardson iteration across subdomain boundaries (App. B.1),
-//     the global cells are solved exactly and without waiting.  Each global
-//     cell has an arrival counter for its global dependencies; a global cell
-//     with none starts a walker, each finished cell increments its targets'
-//     counters, and the thread that completes a counter computes that cell
-//     ("last arriver continues").  Work is O(N), no thread ever waits on
-//     another, and a routing graph with a cycle cannot hang the kernel: its
-//     cells are never reached, which the completion count reports.
+//  1. local phase (fr_d8.cu, fr_halo.cu): every cell whose dependencies all
+//     lie, recursively, inside its tile's extended region is solved exactly in
+//     shared memory in a topological order (Sec. 3.2 shows any such order
+//     gives the same result).  Inner cells with a dependency chain leaving the
+//     region are marked "global" (a bit per cell and a list).
+//  2. global phase (this file, a second kernel): instead of the paper's
+//     Richardson iteration across subdomain boundaries (App. B.1) the global
+//     cells are solved exactly.  Each global cell has an arrival counter for
+//     its global dependencies.  For D8 forward routing (one receiver per cell)
+//     a cell with none starts a walker, each finished cell increments its
+//     receiver's counter, and the thread that completes a counter computes
+//     that cell ("last arriver continues"); no thread ever waits on another.
+//     For the modes where one cell can make several cells ready (MFD forward,
+//     both adjoints) the global cells are processed in rounds instead (see
+//     k_global_levels).  A routing graph with a cycle cannot hang either
+//     kernel: its cells are never reached, which the completion count reports.
 //
-// Values are pulled from dependencies in a fixed neighbour order, so results
-// are bit-reproducible.  Real-valued sums are two-float (fp32 hi + lo); unit
-// rain D8 areas are exact integers.
+// Values are pulled from dependencies in a fixed order, so results are
+// bit-reproducible.  Real-valued sums are two-float (fp32 hi + lo); unit-rain
+// D8 areas are exact integers.
 #pragma once
 
 #include "fr_internal.h"
@@ -41,32 +41,11 @@ struct Eng {
     static constexpr bool kArea = AREA && (M == Mode::FwdD8);
     static constexpr bool kBranch = kMfd || kAdj;         // several targets per cell
     static constexpr bool kD8Fwd = (M == Mode::FwdD8);
-    static constexpr int TX = kTileX, TY = kTileY, NC = TX * TY;
-    static constexpr int RX = TX + 2, RY = TY + 2;
-    static constexpr int NT = 256;
-    static constexpr uint8_t kOobRb = kMfd ? 0 : kSink;
 };
 
-// State byte of a tile cell: bits 0-3 in-tile dependencies still missing,
-// bit 4 global, bit 5 solved locally.
-constexpr uint32_t kG = 0x10u, kDone = 0x20u;
-
-template <class E>
-struct alignas(16) Smem {
-    float vhi[E::kVal ? E::NC : 1];
-    float vlo[E::kVal ? E::NC : 1];
-    float ishi[E::kMfd ? E::NC : 1];
-    float islo[E::kMfd ? E::NC : 1];
-    float z[E::kMfd ? E::RX * E::RY : 1];
-    uint32_t area[E::kArea ? E::NC : 1];
-    uint32_t st[E::NC / 4];
-    uint16_t q[E::kD8Fwd ? 1 : E::NC];
-    uint8_t dm[E::kD8Fwd ? E::NC : 1];
-    uint8_t rb[E::RX * E::RY];
-    int qtail;
-    int64_t work;
-    unsigned long long done;
-};
+// Flag in a tile kernel's per-cell state byte (bits 0-3 count the missing
+// in-region dependencies): the cell's dependencies leave the region.
+constexpr uint32_t kG = 0x10u;
 
 // Receiver mask of a routing byte.  D8 codes above 7 (including FR_SINK) mean
 // no receiver.
@@ -115,12 +94,6 @@ __device__ __forceinline__ void wr_area(const Prob& P, int64_t i, uint64_t v) {
 }
 __device__ __forceinline__ uint32_t cnt_add(const Prob& P, int64_t i, uint32_t n) {
     return FR_OK(i, ncell(P), 5) ? counter_add(P.cnt, i, n) : 0xFFu;
-}
-__device__ __forceinline__ int64_t rd_link(const Prob& P, int64_t i) {
-    return FR_OK(i, ncell(P), 6) ? P.link[i] : -1;
-}
-__device__ __forceinline__ void wr_link(const Prob& P, int64_t i, int64_t v) {
-    if (FR_OK(i, ncell(P), 7)) P.link[i] = v;
 }
 
 template <class E>
@@ -268,7 +241,6 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
     }
 }
 
-constexpr int kStack = 8;
 constexpr unsigned kStatusNoProgress = 5u;
 
 __device__ __forceinline__ bool gbit(const Prob& P, int64_t i) {
@@ -286,71 +258,9 @@ __device__ __forceinline__ uint32_t g_deps_global(const Prob& P, int64_t i) {
     return n;
 }
 
-// Walks downstream (forward) or upstream (adjoint) from a ready global cell.
-// Cells that become ready along the way are continued by this thread: one
-// directly, further ones on a small private stack that spills into a linked
-// list threaded through P.link (each cell becomes ready exactly once, so every
-// cell owns its link slot and nothing needs clearing).  Targets that are not
-// global were solved exactly by their own tile and are skipped.  Returns the
-// number of cells computed.
-template <class E>
-__device__ __noinline__ unsigned long long run_walker(const Prob& P, int64_t start) {
-    unsigned long long n = 0;
-    int64_t stack[E::kBranch ? kStack : 1];
-    int sp = 0;
-    int64_t spill = -1;  // head of the spilled list
-    int64_t cur = start;
-    while (true) {
-        walker_compute<E>(P, cur);
-        ++n;
-        __threadfence();
-        const uint32_t tm = g_targets<E>(P, cur);
-        int64_t next = -1;
-#pragma unroll 1
-        for (int k = 0; k < 8; ++k) {
-            if (!((tm >> k) & 1u)) continue;
-            int64_t t = cur + offi(k, P.nx);
-            // with overlapping tile regions a target may already be final
-            if (!gbit(P, t)) continue;
-            uint32_t got = cnt_add(P, t, 1u);
-            if (got != g_deps_global<E>(P, t)) continue;
-            if (next < 0) {
-                next = t;
-            } else if constexpr (E::kBranch) {
-                if (sp < kStack) {
-                    stack[sp++] = t;
-                } else {
-                    wr_link(P, t, spill);
-                    spill = t;
-                }
-            }
-        }
-        if (next >= 0) {
-            __threadfence();
-            cur = next;
-            continue;
-        }
-        if constexpr (E::kBranch) {
-            if (sp > 0) {
-                __threadfence();
-                cur = stack[--sp];
-                continue;
-            }
-            if (spill >= 0) {
-                __threadfence();
-                cur = spill;
-                spill = rd_link(P, cur);
-                continue;
-            }
-        }
-        break;
-    }
-    return n;
-}
-
 // D8 forward walker: one step per global cell, all loads of a step issued
 // together (the routing bytes of the 3 x 3 window, the cell's rain, the donors'
-// values; then the receiver's window).  Same semantics as run_walker.
+// values; then the receiver's window).
 template <bool W, bool AREA>
 __device__ __noinline__ unsigned long long walker_d8(const Prob& P, int64_t start) {
     unsigned long long n = 0;
@@ -419,454 +329,9 @@ __device__ __noinline__ unsigned long long walker_d8(const Prob& P, int64_t star
     return n;
 }
 
-__device__ __forceinline__ uint32_t st_get(const uint32_t* st, int c) {
-    if (!FR_OK(c, kTileX * kTileY, 20)) return 0x0Fu;
-    return (st[c >> 2] >> (8 * (c & 3))) & 0xFFu;
-}
-
-// In-tile neighbour mask of tile cell (lx, ly) in a tile of tw x th cells.
-__device__ __forceinline__ uint32_t intile_mask(int lx, int ly, int tw, int th) {
-    if (lx > 0 && ly > 0 && lx < tw - 1 && ly < th - 1) return 0xFFu;
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        int xn = lx + offx(k), yn = ly + offy(k);
-        if (xn >= 0 && yn >= 0 && xn < tw && yn < th) m |= 1u << k;
-    }
-    return m;
-}
-
-template <class E>
-__device__ __forceinline__ uint8_t s_rb(const Smem<E>& S, int i) {
-    return FR_OK(i, E::RX * E::RY, 21) ? S.rb[i] : E::kOobRb;
-}
-
-template <class E>
-__device__ __forceinline__ uint32_t s_donors(const Smem<E>& S, int lx, int ly) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if ((recv_mask<E::kMfd>(s_rb<E>(S, (ly + 1 + offy(k)) * E::RX + (lx + 1 + offx(k)))) >> opp(k)) & 1u)
-            m |= 1u << k;
-    return m;
-}
-
-// Receivers of tile cell (lx, ly); gm is the cell's grid mask.
-template <class E>
-__device__ __forceinline__ uint32_t s_recv(const Smem<E>& S, int lx, int ly, uint32_t gm) {
-    return recv_mask<E::kMfd>(s_rb<E>(S, (ly + 1) * E::RX + (lx + 1))) & gm;
-}
-
-template <class E>
-__device__ __forceinline__ uint32_t s_deps(const Smem<E>& S, int lx, int ly, uint32_t gm) {
-    if constexpr (E::kAdj) return s_recv<E>(S, lx, ly, gm);
-    else return s_donors<E>(S, lx, ly);
-}
-
-template <class E>
-__device__ __forceinline__ uint32_t s_targets(const Smem<E>& S, int lx, int ly, uint32_t gm) {
-    if constexpr (E::kAdj) return s_donors<E>(S, lx, ly);
-    else return s_recv<E>(S, lx, ly, gm);
-}
-
-// Warp-aggregated append of tile cell t to the wavefront queue (all 32 lanes
-// must call it together).
-template <class E>
-__device__ __forceinline__ void q_push(Smem<E>& S, bool push, int t) {
-    const unsigned lane = threadIdx.x & 31u;
-    unsigned b = __ballot_sync(0xffffffffu, push);
-    if (!b) return;
-    int base = 0;
-    if (lane == (unsigned)(__ffs(b) - 1)) base = atomicAdd(&S.qtail, __popc(b));
-    base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
-    if (push) {
-        int slot = base + __popc(b & ((1u << lane) - 1u));
-        if (FR_OK(slot, E::NC, 22)) S.q[slot] = (uint16_t)t;
-    }
-}
-
-// Marks a global cell: sets its bit and appends it to the global list.  All
-// 32 lanes call it together; lanes of a warp hold consecutive cells of a tile
-// row, so the bit updates are merged per 32-bit word.
-__device__ __forceinline__ void mark_global(const Prob& P, EngineGlobals* G, bool glob,
-                                            int64_t gi, int pid) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned b = __ballot_sync(0xffffffffu, glob);
-    if (!b) return;
-    const unsigned long long word = glob ? (unsigned long long)(gi >> 5) : ~0ull - lane;
-    const unsigned peers = __match_any_sync(0xffffffffu, word);
-    const unsigned acc = __reduce_or_sync(peers, glob ? (1u << (gi & 31)) : 0u);
-    if (glob && lane == (unsigned)(__ffs(peers) - 1) && FR_OK(gi, ncell(P), 16))
-        atomicOr(P.gbits + (gi >> 5), acc);
-    unsigned long long base = 0;
-    if (lane == (unsigned)(__ffs(b) - 1))
-        base = atomicAdd(&G->glist_count, (unsigned long long)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
-    if (glob) {
-        const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
-        if (FR_OK((int64_t)slot, P.glist_cap, 17))
-            P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
-    }
-}
-
-// Local phase of one tile (generic modes): level-synchronous wavefront.
-template <class E>
-__device__ unsigned long long process_tile(const Prob& P, int pid, int64_t tx, int64_t ty,
-                                           Smem<E>& S, EngineGlobals* G) {
-    constexpr int TX = E::TX, NC = E::NC, RX = E::RX, RY = E::RY, NT = E::NT;
-    const int tid = threadIdx.x;
-    const int64_t x0 = tx * TX, y0 = ty * E::TY;
-    const int tw = (int)(P.nx - x0 < TX ? P.nx - x0 : TX);
-    const int th = (int)(P.ny - y0 < E::TY ? P.ny - y0 : E::TY);
-    unsigned long long done = 0;
-
-    // routing bytes (and elevations) of the tile plus a one-cell ring
-    for (int i = tid; i < RX * RY; i += NT) {
-        int ry = i / RX, rx = i - ry * RX;
-        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
-        bool in = gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny;
-        S.rb[i] = in ? rd_rb(P, gy * P.nx + gx) : E::kOobRb;
-        if constexpr (E::kMfd) S.z[i] = in ? rd_z(P, gy * P.nx + gx) : __int_as_float(0x7f800000);
-    }
-    if (tid == 0) S.qtail = 0;
-    __syncthreads();
-
-    // per-cell state and initial values
-    uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
-    for (int c = tid; c < NC; c += NT) {
-        int ly = c / TX, lx = c - ly * TX;
-        uint8_t b = 0;
-        if (lx < tw && ly < th) {
-            int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
-            const uint32_t gm = grid_mask(x0 + lx, y0 + ly, P.nx, P.ny);
-            uint32_t dep = s_deps<E>(S, lx, ly, gm);
-            uint32_t in = intile_mask(lx, ly, tw, th);
-            b = (uint8_t)(__popc(dep & in) | ((dep & ~in) ? kG : 0u));
-            uint32_t recv = s_recv<E>(S, lx, ly, gm);
-            if constexpr (E::kVal) {
-                df v = init_value<E>(P, gi, recv);
-                S.vhi[c] = v.hi;
-                S.vlo[c] = v.lo;
-            }
-            if constexpr (E::kArea) S.area[c] = 1u;
-            if constexpr (E::kMfd) {
-                float zc = S.z[(ly + 1) * RX + lx + 1];
-                df s = df_make(0.0f);
-#pragma unroll 1
-                for (int k = 0; k < 8; ++k)
-                    if ((recv >> k) & 1u)
-                        s = df_add(s, df_make(mfd_u_call(zc, S.z[(ly + 1 + offy(k)) * RX + lx + 1 + offx(k)], k, P.mc)));
-                df inv = recv ? df_recip(s) : df_make(0.0f);
-                S.ishi[c] = inv.hi;
-                S.islo[c] = inv.lo;
-            }
-        } else {
-            b = 0x0F;  // never reaches zero: outside the grid
-        }
-        stb[c] = b;
-    }
-    __syncthreads();
-    for (int c = tid; c < NC; c += NT) q_push<E>(S, (stb[c] & 0x0Fu) == 0, c);
-    __syncthreads();
-
-    // level-synchronous wavefront over the tile's DAG
-    int begin = 0;
-    while (true) {
-        const int end = S.qtail;
-        __syncthreads();
-        if (begin == end) break;
-        for (int base = begin; base < end; base += NT) {
-            const int i = base + tid;
-            const bool act = i < end;
-            int c = 0, lx = 0, ly = 0;
-            uint32_t tm = 0;
-            bool glob = false;
-            if (act) {
-                c = FR_OK(i, NC, 23) ? S.q[i] : 0;
-                ly = c / TX;
-                lx = c - ly * TX;
-                glob = st_get(S.st, c) & kG;
-                uint32_t in = intile_mask(lx, ly, tw, th);
-                tm = s_targets<E>(S, lx, ly, in) & in;
-                if (!glob) {
-                    uint32_t dep = s_deps<E>(S, lx, ly, in);  // all in tile
-                    if constexpr (E::kVal) {
-                        df v = {S.vhi[c], S.vlo[c]};
-                        float zc = 0.0f;
-                        df myinv = df_make(0.0f);
-                        if constexpr (E::kMfd) {
-                            zc = S.z[(ly + 1) * RX + lx + 1];
-                            myinv = {S.ishi[c], S.islo[c]};
-                        }
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            if (!((dep >> k) & 1u)) continue;
-                            int j = c + offy(k) * TX + offx(k);
-                            if (!FR_OK(j, NC, 24)) continue;
-                            df vj = {S.vhi[j], S.vlo[j]};
-                            if constexpr (E::kMfd) {
-                                float zj = S.z[(ly + 1 + offy(k)) * RX + lx + 1 + offx(k)];
-                                if constexpr (E::kAdj)
-                                    vj = df_mul(mfd_frac(mfd_u_call(zc, zj, k, P.mc), myinv), vj);
-                                else
-                                    vj = df_mul(mfd_frac(mfd_u_call(zj, zc, opp(k), P.mc), df{S.ishi[j], S.islo[j]}), vj);
-                            }
-                            v = df_add(v, vj);
-                        }
-                        S.vhi[c] = v.hi;
-                        S.vlo[c] = v.lo;
-                    }
-                    if constexpr (E::kArea) {
-                        uint32_t a = S.area[c];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            if (((dep >> k) & 1u) && FR_OK(c + offy(k) * TX + offx(k), NC, 25))
-                                a += S.area[c + offy(k) * TX + offx(k)];
-                        S.area[c] = a;
-                    }
-                    atomicOr(&S.st[c >> 2], kDone << (8 * (c & 3)));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                bool push = false;
-                int t = 0;
-                if (((tm >> k) & 1u) && FR_OK(c + offy(k) * TX + offx(k), NC, 26)) {
-                    t = c + offy(k) * TX + offx(k);
-                    uint32_t sh = 8u * (uint32_t)(t & 3);
-                    if (glob) atomicOr(&S.st[t >> 2], kG << sh);
-                    uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
-                    push = ((old >> sh) & 0x0Fu) == 1u;
-                }
-                q_push<E>(S, push, t);
-            }
-        }
-        __syncthreads();
-        begin = end;
-    }
-
-    // publish locally solved cells (row-major, coalesced); list global cells
-    for (int c = tid; c < NC; c += NT) {
-        int ly = c / TX, lx = c - ly * TX;
-        const bool valid = lx < tw && ly < th;
-        const uint32_t b = valid ? st_get(S.st, c) : 0u;
-        const int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
-        mark_global(P, G, valid && (b & kG), gi, pid);
-        if (!valid || !(b & kDone)) continue;
-        ++done;
-        if constexpr (E::kVal) {
-            if (P.out_hi) wr_f(P.out_hi, P, gi, S.vhi[c], 27);
-            bool need_lo = P.lo_full;
-            if (!need_lo) {
-                // a global cell or a cell of another tile will pull this value
-                uint32_t in = intile_mask(lx, ly, tw, th);
-                uint32_t tm = s_targets<E>(S, lx, ly, grid_mask(x0 + lx, y0 + ly, P.nx, P.ny));
-                if (tm & ~in) need_lo = true;
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (((tm & in) >> k) & 1u)
-                        if (st_get(S.st, c + offy(k) * TX + offx(k)) & kG) need_lo = true;
-            }
-            if (need_lo) wr_f(P.out_lo, P, gi, S.vlo[c], 28);
-        }
-        if constexpr (E::kArea) wr_area(P, gi, S.area[c]);
-    }
-    return done;
-}
-
-// --------------------------------------------------------- D8 forward tile
-// Specialised local phase for D8 forward routing: every tile cell has at most
-// one receiver, so a finished cell is continued by the thread that completes
-// its receiver's count ("last arriver", shared-memory atomics), with no
-// rounds and no barriers inside the solve.
-template <class E>
-__device__ unsigned long long process_tile_d8(const Prob& P, int pid, int64_t tx, int64_t ty,
-                                              Smem<E>& S, EngineGlobals* G) {
-    constexpr int TX = E::TX, NC = E::NC, RX = E::RX, RY = E::RY, NT = E::NT;
-    const int tid = threadIdx.x;
-    const int64_t x0 = tx * TX, y0 = ty * E::TY;
-    const int tw = (int)(P.nx - x0 < TX ? P.nx - x0 : TX);
-    const int th = (int)(P.ny - y0 < E::TY ? P.ny - y0 : E::TY);
-    unsigned long long done = 0;
-
-    for (int i = tid; i < RX * RY; i += NT) {
-        int ry = i / RX, rx = i - ry * RX;
-        int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
-        bool in = gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny;
-        uint8_t code = in ? rd_rb(P, gy * P.nx + gx) : kSink;
-        if (code < 8) {  // receivers outside the grid act as none
-            int64_t xr = gx + offx(code), yr = gy + offy(code);
-            if (xr < 0 || yr < 0 || xr >= P.nx || yr >= P.ny) code = kSink;
-        } else {
-            code = kSink;
-        }
-        S.rb[i] = code;
-    }
-    __syncthreads();
-
-    uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
-    for (int c = tid; c < NC; c += NT) {
-        int ly = c / TX, lx = c - ly * TX;
-        uint8_t b = 0x0F;
-        if (lx < tw && ly < th) {
-            const int r = (ly + 1) * RX + lx + 1;
-            uint32_t dm = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                dm |= (uint32_t)(S.rb[r + offy(k) * RX + offx(k)] == (uint8_t)opp(k)) << k;
-            const uint32_t in = intile_mask(lx, ly, tw, th);
-            b = (uint8_t)(__popc(dm & in) | ((dm & ~in) ? kG : 0u));
-            S.dm[c] = (uint8_t)(dm & in);
-            const int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
-            if constexpr (E::kVal) {
-                S.vhi[c] = P.init ? rd_in(P.init, P, gi, 8) : 1.0f;
-                S.vlo[c] = 0.0f;
-            }
-            if constexpr (E::kArea) S.area[c] = 1u;
-        }
-        stb[c] = b;
-    }
-    __syncthreads();
-
-    // chain walks from the cells whose in-tile donors are all... none
-    for (int c0 = tid; c0 < NC; c0 += NT) {
-        {
-            int ly = c0 / TX, lx = c0 - ly * TX;
-            if (lx >= tw || ly >= th || S.dm[c0] != 0) continue;
-        }
-        int c = c0;
-        while (true) {
-            const int ly = c / TX, lx = c - ly * TX;
-            const uint32_t b = st_get(S.st, c);
-            const bool glob = b & kG;
-            if (!glob) {
-                const uint32_t dm = S.dm[c];
-                if constexpr (E::kVal) {
-                    df v = {S.vhi[c], S.vlo[c]};
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if ((dm >> k) & 1u) {
-                            const int j = c + offy(k) * TX + offx(k);
-                            v = df_add(v, df{S.vhi[j], S.vlo[j]});
-                        }
-                    S.vhi[c] = v.hi;
-                    S.vlo[c] = v.lo;
-                }
-                if constexpr (E::kArea) {
-                    uint32_t a = S.area[c];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if ((dm >> k) & 1u) a += S.area[c + offy(k) * TX + offx(k)];
-                    S.area[c] = a;
-                }
-            }
-            const uint8_t code = S.rb[(ly + 1) * RX + lx + 1];
-            atomicOr(&S.st[c >> 2], kDone << (8 * (c & 3)));
-            if (code >= 8) break;
-            const int xr = lx + offx(code), yr = ly + offy(code);
-            if (xr < 0 || yr < 0 || xr >= tw || yr >= th) break;  // leaves the tile
-            const int t = yr * TX + xr;
-            const uint32_t sh = 8u * (uint32_t)(t & 3);
-            if (glob) atomicOr(&S.st[t >> 2], kG << sh);
-            __threadfence_block();
-            const uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
-            if (((old >> sh) & 0x0Fu) != 1u) break;
-            __threadfence_block();
-            c = t;
-        }
-    }
-    __syncthreads();
-
-    for (int c = tid; c < NC; c += NT) {
-        int ly = c / TX, lx = c - ly * TX;
-        const bool valid = lx < tw && ly < th;
-        const uint32_t b = valid ? st_get(S.st, c) : 0u;
-        const int64_t gi = (y0 + ly) * P.nx + (x0 + lx);
-        mark_global(P, G, valid && (b & kG), gi, pid);
-        if (!valid || (b & kG) || !(b & kDone)) continue;
-        ++done;
-        if constexpr (E::kVal) {
-            wr_f(P.out_hi, P, gi, S.vhi[c], 27);
-            bool need_lo = P.lo_full;
-            if (!need_lo) {
-                const uint8_t code = S.rb[(ly + 1) * RX + lx + 1];
-                if (code < 8) {
-                    const int xr = lx + offx(code), yr = ly + offy(code);
-                    need_lo = (xr < 0 || yr < 0 || xr >= tw || yr >= th) ||
-                              (st_get(S.st, yr * TX + xr) & kG);
-                }
-            }
-            if (need_lo) wr_f(P.out_lo, P, gi, S.vlo[c], 28);
-        }
-        if constexpr (E::kArea) wr_area(P, gi, S.area[c]);
-    }
-    return done;
-}
-
-template <class E>
-__device__ __forceinline__ unsigned long long solve_tile(const Prob& P, int pid, int64_t tx,
-                                                         int64_t ty, Smem<E>& S, EngineGlobals* G) {
-    if constexpr (E::kD8Fwd) return process_tile_d8<E>(P, pid, tx, ty, S, G);
-    else return process_tile<E>(P, pid, tx, ty, S, G);
-}
-
-// Block-wide sum of per-thread counts, added once per CTA.
-template <class E>
-__device__ void add_done(Smem<E>& S, unsigned long long done, EngineGlobals* G) {
-    for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
-    if (threadIdx.x == 0) S.done = 0;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0 && done) atomicAdd(&S.done, done);
-    __syncthreads();
-    if (threadIdx.x == 0 && S.done) atomicAdd(&G->done_cells, S.done);
-}
-
-// Local phase over all tiles of one problem (one CTA per tile).
-template <Mode M, bool W, bool AREA>
-__global__ void __launch_bounds__(256) k_local(Prob P, EngineGlobals* G) {
-    using E = Eng<M, W, AREA>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<E>& S = *reinterpret_cast<Smem<E>*>(smem_raw);
-    const int64_t tile = blockIdx.x;
-    const int64_t ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
-    add_done<E>(S, solve_tile<E>(P, 0, tx, ty, S, G), G);
-}
-
-// Local phase, batched: CTAs claim tiles of any problem from a global counter.
-// tile_prefix[p] is the first tile of problem p.
-template <Mode M, bool W, bool AREA>
-__global__ void __launch_bounds__(256) k_local_batch(const Prob* __restrict__ probs,
-                                                     const int64_t* __restrict__ tile_prefix,
-                                                     int nprob, int64_t total_tiles,
-                                                     EngineGlobals* G) {
-    using E = Eng<M, W, AREA>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<E>& S = *reinterpret_cast<Smem<E>*>(smem_raw);
-    unsigned long long done = 0;
-    while (true) {
-        if (threadIdx.x == 0) S.work = (int64_t)atomicAdd(&G->work_next, 1ull);
-        __syncthreads();
-        const int64_t w = S.work;
-        __syncthreads();
-        if (w >= total_tiles) break;
-        int lo = 0, hi = nprob - 1;  // last p with tile_prefix[p] <= w
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (tile_prefix[mid] <= w) lo = mid;
-            else hi = mid - 1;
-        }
-        const Prob P = probs[lo];
-        const int64_t lt = w - tile_prefix[lo];
-        const int64_t ty = lt / P.tiles_x, tx = lt - ty * P.tiles_x;
-        done += solve_tile<E>(P, lo, tx, ty, S, G);
-        __syncthreads();
-    }
-    add_done<E>(S, done, G);
-}
-
-// Global phase: grid-stride over the global-cell list; cells with no global
-// dependency start walkers.  The last CTA to finish checks that every cell of
-// every problem was computed.
+// Global phase of D8 forward routing: grid-stride over the global-cell list;
+// cells with no global dependency start walkers.  The last CTA to finish
+// checks that every cell of every problem was computed.
 template <Mode M, bool W, bool AREA>
 __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, Prob single,
                                                 EngineGlobals* G, unsigned long long total_cells) {
@@ -882,8 +347,8 @@ __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, 
         const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
         const Prob& P = probs ? probs[pid] : single;
         if (g_deps_global<E>(P, cell) != 0) continue;
-        if constexpr (E::kD8Fwd) done += walker_d8<W, AREA>(P, cell);
-        else done += run_walker<E>(P, cell);
+        static_assert(E::kD8Fwd, "branching modes use k_global_levels");
+        done += walker_d8<W, AREA>(P, cell);
     }
     for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
     if (threadIdx.x == 0) s_done = 0;
@@ -1093,11 +558,6 @@ cudaError_t launch_global(const Prob* probs, const Prob& single, EngineGlobals* 
         return cudaLaunchCooperativeKernel((const void*)k_global_levels<M, W, AREA>, dim3(grid),
                                            dim3(256), args, 0, s);
     }
-}
-
-template <Mode M, bool W, bool AREA>
-constexpr size_t engine_smem() {
-    return sizeof(Smem<Eng<M, W, AREA>>);
 }
 
 }  // namespace fr

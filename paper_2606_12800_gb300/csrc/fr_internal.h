@@ -32,14 +32,12 @@ struct Prob {
     float* out_lo;         // value trailing word (user output or workspace)
     uint64_t* area;        // D8 forward unit-rain areas or NULL
     uint32_t* cnt;         // packed byte arrival counters, zeroed before the launch
-    int64_t* link;         // per-cell spill links of the walkers (no init needed)
+    int64_t* link;         // 8 B/cell scratch: frontier buffer of the global rounds
     uint32_t* gbits;       // one bit per cell: "global" (solved by the walkers), zeroed
     unsigned long long* glist;  // compact list of global cells (pid << 40 | cell)
     int64_t glist_cap;     // capacity of glist (entries)
     MfdConst mc;
     int32_t lo_full;       // out_lo is a user output: write it for every cell
-    int32_t tiles_x;       // number of CTA tiles along x
-    int64_t tile_base;     // first global work index of this problem (batched)
 };
 
 // Device-wide bookkeeping kept at the start of the workspace; zeroed (with
@@ -63,14 +61,7 @@ static_assert(sizeof(EngineGlobals) == 128, "globals block is 128 bytes (256 res
 
 enum class Mode : int { FwdD8 = 0, FwdMfd = 1, AdjD8 = 2, AdjMfd = 3 };
 
-// Tile engine launches (fr_accumulate.cu): the tile kernel (local phase) and
-// the walker kernel (global phase), in stream order.
-cudaError_t launch_engine(Mode mode, bool want_w, bool want_area, const Prob& prob,
-                          EngineGlobals* g, cudaStream_t s);
-cudaError_t launch_engine_batch(Mode mode, bool want_w, bool want_area, const Prob* probs_dev,
-                                const int64_t* tile_prefix_dev, int32_t nprob,
-                                int64_t total_tiles, unsigned long long total_cells,
-                                EngineGlobals* g, int grid, cudaStream_t s);
+// Grid of the D8 forward walker kernel (fr_accumulate.cu).
 int walker_grid();
 // D8 forward: halo-tile local phase (fr_d8.cu) + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
@@ -104,10 +95,6 @@ constexpr int kRecvTileY = 16;
 __host__ __device__ inline int64_t receiver_tiles(int64_t nx, int64_t ny) {
     return ((nx + kRecvTileX - 1) / kRecvTileX) * ((ny + kRecvTileY - 1) / kRecvTileY);
 }
-
-// Engine tile shape (cells) of the generic tile kernel (adjoints).
-constexpr int kTileX = 64;
-constexpr int kTileY = 32;
 
 // Inner tiles of the halo kernels: D8 geometry 0 is kD8TileX x kD8TileY,
 // geometry 1 half as wide; MFD uses kMfdTileX x kMfdTileY.
