@@ -8,6 +8,26 @@ namespace {
 // ---------------------------------------------------------------- mass balance
 constexpr int MB_NT = 256;
 
+// Bit i set where byte i of the 16 routing bytes in v marks a sink (D8 code
+// 0xFF, MFD empty mask).
+template <bool MFD>
+__device__ __forceinline__ uint32_t sink_bits16(const uint4 v) {
+    const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t zb = zero_bytes(MFD ? words[q] : ~words[q]);  // 0x80 per sink byte
+        zb >>= 7;                                               // bit 0 of each byte
+        bits |= ((zb & 1u) | ((zb >> 7) & 2u) | ((zb >> 14) & 4u) | ((zb >> 21) & 8u)) << (4 * q);
+    }
+    return bits;
+}
+
+// Partial sums of one block: rain (two-float), water at sinks (two-float) and
+// area at sinks (exact).  Each thread takes chunks of 16 cells (16-byte routing
+// load, four 16-byte rain loads; the rain of a chunk is summed pairwise) and
+// then gathers only the chunk's sinks.  Grid-stride over chunks in a fixed
+// order, so the result does not depend on scheduling.
 template <bool MFD>
 __global__ void __launch_bounds__(MB_NT) k_mass_partial(int64_t n, const uint8_t* __restrict__ rb,
                                                         const float* __restrict__ rain,
@@ -18,14 +38,33 @@ __global__ void __launch_bounds__(MB_NT) k_mass_partial(int64_t n, const uint8_t
     df sw = df_make(0.0f), sr = df_make(0.0f);
     unsigned long long sa = 0;
     const int64_t stride = (int64_t)gridDim.x * MB_NT;
-    for (int64_t i = (int64_t)blockIdx.x * MB_NT + threadIdx.x; i < n; i += stride) {
-        uint8_t b = rb[i];
-        bool sink = MFD ? (b == 0) : (b == kSink);
-        sr = df_add(sr, df_make(rain ? rain[i] : 1.0f));
-        if (sink) {
-            if (w) sw = df_add(sw, df{w[i], w_lo ? w_lo[i] : 0.0f});
-            if (area) sa += area[i];
+    const int64_t first = (int64_t)blockIdx.x * MB_NT + threadIdx.x;
+    const bool vec = ((uintptr_t)rb & 15) == 0 && (!rain || ((uintptr_t)rain & 15) == 0);
+    const int64_t nchunk = vec ? n / 16 : 0;
+    auto sink_add = [&](int64_t i) {
+        if (w) sw = df_add(sw, df{__ldg(w + i), w_lo ? __ldg(w_lo + i) : 0.0f});
+        if (area) sa += __ldg(area + i);
+    };
+    for (int64_t c = first; c < nchunk; c += stride) {
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(rb) + c);
+        if (rain) {
+            const float4* r4 = reinterpret_cast<const float4*>(rain) + 4 * c;
+            const float4 a0 = __ldg(r4), a1 = __ldg(r4 + 1), a2 = __ldg(r4 + 2), a3 = __ldg(r4 + 3);
+            const df p0 = df_add(df_add(df_make(a0.x), df_make(a0.y)), df_add(df_make(a0.z), df_make(a0.w)));
+            const df p1 = df_add(df_add(df_make(a1.x), df_make(a1.y)), df_add(df_make(a1.z), df_make(a1.w)));
+            const df p2 = df_add(df_add(df_make(a2.x), df_make(a2.y)), df_add(df_make(a2.z), df_make(a2.w)));
+            const df p3 = df_add(df_add(df_make(a3.x), df_make(a3.y)), df_add(df_make(a3.z), df_make(a3.w)));
+            sr = df_add(sr, df_add(df_add(p0, p1), df_add(p2, p3)));
+        } else {
+            sr = df_add(sr, df_make(16.0f));
         }
+        for (uint32_t m = sink_bits16<MFD>(b); m; m &= m - 1) sink_add(16 * c + (__ffs(m) - 1));
+    }
+    // cells after the last whole chunk (or all cells without the vector path)
+    for (int64_t i = 16 * nchunk + first; i < n; i += stride) {
+        const uint8_t bb = rb[i];
+        sr = df_add(sr, df_make(rain ? rain[i] : 1.0f));
+        if (MFD ? (bb == 0) : (bb == kSink)) sink_add(i);
     }
     double v0 = (double)sw.hi + (double)sw.lo, v1 = (double)sr.hi + (double)sr.lo;
     for (int o = 16; o; o >>= 1) {

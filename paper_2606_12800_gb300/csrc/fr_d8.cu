@@ -70,11 +70,6 @@ __device__ __forceinline__ uint32_t stget(const uint32_t* st, int c) {
     return (st[c >> 2] >> (8 * (c & 3))) & 0xFFu;
 }
 
-// 0x80 in each byte of x that is zero, 0 elsewhere (exact, no carries between bytes).
-__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
-    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
-}
-
 // Per-byte population count.
 __device__ __forceinline__ uint32_t popc_bytes(uint32_t x) {
     x = x - ((x >> 1) & 0x55555555u);

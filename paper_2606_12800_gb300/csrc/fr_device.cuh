@@ -114,6 +114,25 @@ __device__ __forceinline__ uint8_t d8_code(float zc, const float (&zn)[8], float
     return code;
 }
 
+// The same selection without branches, for the rule fixed at compile time:
+// d = fl32(zc - zk) > 0 exactly when zk < zc (a difference of two floats is
+// zero only if they are equal; infinities and NaN compare false as above).
+template <bool LOWEST>
+__device__ __forceinline__ uint32_t d8_code_sel(float zc, const float (&zn)[8], float c_orth,
+                                                float c_diag) {
+    float best = -1.0f;
+    uint32_t code = kSink;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float d = __fsub_rn(zc, zn[k]);
+        const float s = LOWEST ? d : __fmul_rn(d, k < 4 ? c_orth : c_diag);
+        const bool take = (d > 0.0f) & (s > best);
+        best = take ? s : best;
+        code = take ? (uint32_t)k : code;
+    }
+    return code;
+}
+
 // ------------------------------------------------------------ MFD weights
 // Reciprocal distances 1/d_k as two-float, set on the host from FP64, and the
 // exponent p split into its integer part pn and fraction pf (FP64, then
@@ -221,6 +240,11 @@ __device__ __forceinline__ df mfd_frac(float u, df inv_s) {
     float e = __fmaf_rn(u, inv_s.hi, -p);
     e = __fmaf_rn(u, inv_s.lo, e);
     return df_norm(p, e);
+}
+
+// 0x80 in each byte of x that is zero, 0 elsewhere (exact, no carries between bytes).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
+    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
 }
 
 // ------------------------------------------------------------ byte counters

@@ -49,7 +49,7 @@ __device__ __forceinline__ void tile_origin(int64_t nx, int64_t& x0, int64_t& y0
 // D8 codes of RTX x RTY tile cells; each thread computes four consecutive
 // cells of a row from a 3 x 6 register window.  Tiles away from the grid
 // boundary skip all edge and bounds tests.
-template <bool INDEG>
+template <bool INDEG, bool LOWEST>
 __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_t nx, int64_t ny,
                                              float c_orth, float c_diag, uint32_t flags,
                                              uint8_t* __restrict__ dir,
@@ -57,14 +57,17 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
                                              int64_t y0) {
     __shared__ float zs[HX * HY];
     __shared__ uint8_t ds[RX * RY];
-    const bool lowest = flags & kD8Lowest;
+    const bool lowest = LOWEST;
     const bool edge_route = flags & kEdgeRoute;
     const bool interior = x0 >= 2 && y0 >= 2 && x0 + RTX + 2 <= nx && y0 + RTY + 2 <= ny;
     if (interior) {
+        // row by row: a warp per row, lanes along it
         const float* base = z + (y0 - 2) * nx + (x0 - 2);
-        for (int i = threadIdx.x; i < HX * HY; i += RNT) {
-            const int ly = i / HX, lx = i - ly * HX;
-            zs[i] = __ldg(base + (int64_t)ly * nx + lx);
+        const int lane = threadIdx.x & 31;
+        for (int ly = threadIdx.x >> 5; ly < HY; ly += RNT / 32) {
+            const float* row = base + (int64_t)ly * nx;
+#pragma unroll
+            for (int lx = lane; lx < HX; lx += 32) zs[ly * HX + lx] = __ldg(row + lx);
         }
     } else {
         load_z_tile(zs, z, nx, ny, x0, y0);
@@ -83,7 +86,7 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
         for (int q = 0; q < 4; ++q) {
             const float zn[8] = {w[1][q + 2], w[0][q + 1], w[1][q], w[2][q + 1],
                                  w[0][q + 2], w[0][q], w[2][q], w[2][q + 2]};
-            uint8_t code = d8_code(w[1][q + 1], zn, c_orth, c_diag, lowest);
+            uint8_t code = (uint8_t)d8_code_sel<LOWEST>(w[1][q + 1], zn, c_orth, c_diag);
             if (!interior) {  // interior tiles hold no edge cell and no cell off the grid
                 const int64_t gx = x0 + qx + q, gy = y0 + r;
                 if (gx >= nx || gy >= ny || (!edge_route && is_edge(gx, gy, nx, ny))) code = kSink;
@@ -135,14 +138,14 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
     }
 }
 
-template <bool INDEG>
+template <bool INDEG, bool LOWEST>
 __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ z, int64_t nx,
                                                       int64_t ny, float c_orth, float c_diag,
                                                       uint32_t flags, uint8_t* __restrict__ dir,
                                                       uint8_t* __restrict__ indeg) {
     int64_t x0, y0;
     tile_origin(nx, x0, y0);
-    recv_d8_tile<INDEG>(z, nx, ny, c_orth, c_diag, flags, dir, indeg, x0, y0);
+    recv_d8_tile<INDEG, LOWEST>(z, nx, ny, c_orth, c_diag, flags, dir, indeg, x0, y0);
 }
 
 template <bool FRAC, bool INDEG>
@@ -249,9 +252,12 @@ __global__ void __launch_bounds__(RNT) k_receivers_batch(int kind, const Prob* _
         const int64_t lt = w - prefix[lo];
         const int64_t tiles_x = (P.nx + RTX - 1) / RTX;
         const int64_t ty = lt / tiles_x, tx = lt - ty * tiles_x;
-        if (kind == 0)
-            recv_d8_tile<false>(P.z, P.nx, P.ny, P.mc.co_hi, P.mc.cd_hi, flags,
-                                const_cast<uint8_t*>(P.rb), nullptr, tx * RTX, ty * RTY);
+        if (kind == 0 && (flags & kD8Lowest))
+            recv_d8_tile<false, true>(P.z, P.nx, P.ny, P.mc.co_hi, P.mc.cd_hi, flags,
+                                      const_cast<uint8_t*>(P.rb), nullptr, tx * RTX, ty * RTY);
+        else if (kind == 0)
+            recv_d8_tile<false, false>(P.z, P.nx, P.ny, P.mc.co_hi, P.mc.cd_hi, flags,
+                                       const_cast<uint8_t*>(P.rb), nullptr, tx * RTX, ty * RTY);
         else
             recv_mfd_tile<false, false>(P.z, P.nx, P.ny, P.mc, flags, const_cast<uint8_t*>(P.rb),
                                         nullptr, nullptr, tx * RTX, ty * RTY);
@@ -276,10 +282,15 @@ cudaError_t launch_receivers_d8(const float* z, int64_t nx, int64_t ny, double d
     const unsigned grid = (unsigned)(((nx + RTX - 1) / RTX) * ((ny + RTY - 1) / RTY));
     float co = (float)(1.0 / dx);
     float cd = (float)(1.0 / (std::sqrt(2.0) * dx));
-    if (indeg)
-        k_receivers_d8<true><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, indeg);
+    const bool lowest = flags & kD8Lowest;
+    if (indeg && lowest)
+        k_receivers_d8<true, true><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, indeg);
+    else if (indeg)
+        k_receivers_d8<true, false><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, indeg);
+    else if (lowest)
+        k_receivers_d8<false, true><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, nullptr);
     else
-        k_receivers_d8<false><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, nullptr);
+        k_receivers_d8<false, false><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, nullptr);
     return cudaGetLastError();
 }
 
