@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the MFD/batch/adjoint rows")
+    ap.add_argument("--rows", default="slope_split,batched,adjoint,d8_32768",
+                    help="comma-separated extra rows to run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
@@ -284,7 +286,7 @@ def main():
 
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = extra_rows(api, L, dev, peak)
+        extra = extra_rows(api, L, dev, peak, set(args.rows.split(",")))
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -344,8 +346,9 @@ def cpu_baseline(z_np, r_np):
                 "sample": "failed: %s" % e}
 
 
-def extra_rows(api, L, dev, peak):
-    """Slope-split route (8192^2) and D8 adjoint, each timed with events."""
+def extra_rows(api, L, dev, peak, want):
+    """The other workloads, each timed with CUDA events: slope-split route
+    (8192^2), the batched route, the MFD adjoint (16384^2) and D8 on 32768^2."""
     import torch
     from paper_2606_12800_gb300 import inputs
     rows = {}
@@ -367,24 +370,29 @@ def extra_rows(api, L, dev, peak):
             ms.append(a.elapsed_time(b))
         return statistics.mean(ms)
 
-    n = MFD_SIDE
-    zt = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=SEED + 2, device="cuda")
-    mask = torch.empty((n, n), dtype=torch.uint8, device=dev)
-    w = torch.empty((n, n), dtype=torch.float32, device=dev)
+    if "slope_split" in want:
+        n = MFD_SIDE
+        zt = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=SEED + 2, device="cuda")
 
-    def mfd():
-        m = api.receivers_mfd(zt, DX, 1.1)
-        mask.copy_(m)
-        Rm = api.routing_mfd(mask, zt, DX, 1.1)
-        return api.accumulate(Rm, None, want_w=True, device=dev)
-    ms = timed(mfd)
-    rows["slope_split"] = {"value": n * n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
-                           "workload": "MFD p=1.1, %dx%d fractal DEM beta=2.2 no tilt, unit rain" % (n, n),
-                           "hbm_frac": (n * n * 8) / (ms * 1e-3) / 1e9 / peak}
-    del zt, mask, w
-    torch.cuda.empty_cache()
-    rows["batched"] = batch_rows(api, L, dev)
-    torch.cuda.empty_cache()
+        def mfd():
+            m = api.receivers_mfd(zt, DX, 1.1)
+            Rm = api.routing_mfd(m, zt, DX, 1.1)
+            return api.accumulate(Rm, None, want_w=True, device=dev)
+        ms = timed(mfd)
+        rows["slope_split"] = {"value": n * n / (ms * 1e-3), "unit": "cells/s", "ms": ms,
+                               "workload": "MFD p=1.1, %dx%d fractal DEM beta=2.2 no tilt, unit rain" % (n, n),
+                               "hbm_frac": (n * n * 8) / (ms * 1e-3) / 1e9 / peak}
+        del zt
+        torch.cuda.empty_cache()
+    if "batched" in want:
+        rows["batched"] = batch_rows(api, L, dev)
+        torch.cuda.empty_cache()
+    if "adjoint" in want:
+        rows["adjoint"] = adjoint_row(api, dev, peak, timed)
+        torch.cuda.empty_cache()
+    if "d8_32768" in want:
+        rows["d8_32768"] = d8_large_row(api, L, dev, peak, timed)
+        torch.cuda.empty_cache()
     return rows
 
 
