@@ -459,7 +459,7 @@ def batch_rows(api, L, dev):
             row["graph_error"] = str(e)[:200]
         st = int(L.fr_get_status(wsp, need, api._stream()))
         row["status"] = st
-        tws = api.workspace(2048, 2048, dev)
+        tws = api.workspace(2048, 2048, dev, mfd=(kind == "mfd"))
         twsp, twsn = P(tws.data_ptr()), tws.numel()
 
         def per_tile():

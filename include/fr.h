@@ -81,6 +81,9 @@ typedef enum {
 
 #define FR_SINK 0xFFu
 
+/* Largest MFD slope exponent p accepted (the weights take floor(p) products). */
+#define FR_MFD_MAX_P 64.0
+
 typedef enum { FR_ROUTING_D8 = 0, FR_ROUTING_MFD = 1 } fr_routing_kind;
 
 /* Operation codes for fr_workspace_size. */
@@ -89,7 +92,10 @@ typedef enum {
     FR_OP_ACCUMULATE = 1,
     FR_OP_ADJOINT = 2,
     FR_OP_MASS_BALANCE = 3,
-    FR_OP_ROUTE = 4 /* receivers + accumulate in one call (fr_route_d8/_mfd) */
+    FR_OP_ROUTE = 4, /* receivers + accumulate in one call (fr_route_d8) */
+    FR_OP_MFD = 5    /* any operation on an MFD routing (fr_accumulate, fr_route_mfd,
+                        fr_route_adjoint): the common workspace plus the fractions of
+                        every cell, 32 bytes per cell */
 } fr_op;
 
 /*
@@ -113,9 +119,12 @@ fr_status fr_receivers_d8(const float* dem, int64_t nx, int64_t ny, double dx, u
  *   mask_out  [ny*nx] uint8: bit k set iff neighbour k receives water
  *             (0 = sink).
  *   frac_out  [ny*nx*8] float32 or NULL: f_k per cell and code, 0 where bit k
- *             is clear.  Computed in fp32 with a compensated normaliser.
+ *             is clear: f_k = u_k * (1/S) with the weights u_k = s_k^p, their
+ *             sum S in a fixed pairwise order and 1/S as two-float, each f_k
+ *             rounded once to fp32.  These are the fractions every MFD
+ *             operation of this library uses.
  *   indeg_out [ny*nx] uint8 or NULL: number of donors.
- *   p         exponent, finite, > 0 (1.1 in the benchmark configuration).
+ *   p         exponent, 0 < p <= FR_MFD_MAX_P (1.1 in the benchmark configuration).
  */
 fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
                            uint32_t flags, uint8_t* mask_out, float* frac_out,
@@ -129,8 +138,9 @@ typedef struct {
     int64_t nx, ny;
     const uint8_t* dir;   /* D8: [ny*nx] codes from fr_receivers_d8 */
     const uint8_t* mask;  /* MFD: [ny*nx] receiver masks from fr_receivers_mfd */
-    const float* dem;     /* MFD: [ny*nx] elevations; fractions are recomputed
-                             from them (same arithmetic as fr_receivers_mfd) */
+    const float* dem;     /* MFD: [ny*nx] elevations; the fractions are computed
+                             from them into the workspace (the arithmetic of
+                             fr_receivers_mfd's frac_out) */
     double dx;            /* MFD: grid spacing */
     double p;             /* MFD: slope exponent */
     uint32_t flags;       /* MFD: the flags given to fr_receivers_mfd */
@@ -151,7 +161,8 @@ typedef struct {
  *   area_out  [ny*nx] uint64 or NULL: D8 only -- unit-rain drainage area in
  *             cells (Sec. 1, "a note on terminology"), exact.  Ignores rain.
  * At least one output must be non-NULL.  Requires ws of
- * fr_workspace_size(FR_OP_ACCUMULATE, nx, ny, flags) bytes.
+ * fr_workspace_size(FR_OP_ACCUMULATE, nx, ny, flags) bytes for D8,
+ * fr_workspace_size(FR_OP_MFD, nx, ny, flags) for MFD.
  * A routing graph with a cycle leaves FR_ERR_NO_PROGRESS in the status word.
  */
 fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_out,
@@ -195,7 +206,9 @@ fr_status fr_route_d8_noalloc(const float* dem, int64_t nx, int64_t ny, double d
                               const float* rain, float* w_out, float* w_lo_out,
                               uint64_t* area_out, uint8_t* dir_out, void* stream);
 
-/* Receivers + accumulation in one call (MFD).  mask_out may be NULL. */
+/* Receivers + accumulation in one call (MFD): masks and fractions in one
+ * pass, then the accumulation.  mask_out may be NULL.
+ * Workspace: fr_workspace_size(FR_OP_MFD, nx, ny, flags). */
 fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, double p,
                        uint32_t flags, const float* rain, float* w_out, float* w_lo_out,
                        uint8_t* mask_out, void* ws, size_t ws_bytes, void* stream);
@@ -214,7 +227,8 @@ fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, doub
  *   dLdr_out  [ny*nx] float32 (required).
  *   dLdz_out  [ny*nx] float32 or NULL; must be NULL for D8 (the D8 routing is
  *             piecewise constant in z, so dL/dz = 0 almost everywhere).
- * Workspace: fr_workspace_size(FR_OP_ADJOINT, nx, ny, flags).
+ * Workspace: fr_workspace_size(FR_OP_ADJOINT, nx, ny, flags) for D8,
+ * fr_workspace_size(FR_OP_MFD, nx, ny, flags) for MFD.
  */
 fr_status fr_route_adjoint(const fr_routing* routing, const float* w, const float* w_lo,
                            const float* dLdw, float* dLdr_out, float* dLdz_out, void* ws,

@@ -39,6 +39,7 @@ FR_OP_ACCUMULATE = 1
 FR_OP_ADJOINT = 2
 FR_OP_MASS_BALANCE = 3
 FR_OP_ROUTE = 4
+FR_OP_MFD = 5
 
 # Largest grid (cells) fr_route_d8_noalloc accepts.
 FR_NOALLOC_MAX_CELLS = 1 << 20

@@ -13,7 +13,7 @@ from typing import Dict, Optional
 import torch
 
 from . import _lib
-from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_ROUTE, check, fr_routing, load)
+from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_MFD, FR_OP_ROUTE, check, fr_routing, load)
 
 _ws_cache: Dict[int, torch.Tensor] = {}
 
@@ -37,11 +37,12 @@ def _check_grid(t: torch.Tensor, dtype, name: str):
         raise ValueError("%s must be contiguous" % name)
 
 
-def workspace(nx: int, ny: int, device=None) -> torch.Tensor:
-    """A cached workspace large enough for any operation on an nx-by-ny grid."""
+def workspace(nx: int, ny: int, device=None, mfd: bool = False) -> torch.Tensor:
+    """A cached workspace large enough for any operation on an nx-by-ny grid
+    (with room for the fractions of an MFD routing when ``mfd``)."""
     dev = torch.device(device if device is not None else "cuda")
     idx = dev.index if dev.index is not None else torch.cuda.current_device()
-    need = int(load().fr_workspace_size(FR_OP_ROUTE, nx, ny, 0))
+    need = int(load().fr_workspace_size(FR_OP_MFD if mfd else FR_OP_ROUTE, nx, ny, 0))
     if need == 0:
         raise ValueError("invalid grid size %dx%d" % (nx, ny))
     ws = _ws_cache.get(idx)
@@ -112,7 +113,7 @@ def accumulate(R: fr_routing, rain: Optional[torch.Tensor] = None, want_w: bool 
     w = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_w else None
     lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
     a = torch.empty((ny, nx), dtype=torch.int64, device=dev) if want_area else None
-    ws = workspace(nx, ny, dev)
+    ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
     check(load().fr_accumulate(ctypes.byref(R), _p(rain), _p(w), _p(lo), _p(a), _p(ws),
                                ws.numel(), _stream()), "fr_accumulate")
     if w is not None:
@@ -166,7 +167,7 @@ def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
     w = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
     m = torch.empty((ny, nx), dtype=torch.uint8, device=dev) if want_mask else None
-    ws = workspace(nx, ny, dev)
+    ws = workspace(nx, ny, dev, mfd=True)
     check(load().fr_route_mfd(_p(dem_d), nx, ny, dx, p, flags, _p(rain_d), _p(w), _p(lo), _p(m),
                               _p(ws), ws.numel(), _stream()), "fr_route_mfd")
     out = {k: v for k, v in (("w", w), ("w_lo", lo), ("mask", m)) if v is not None}
@@ -183,7 +184,7 @@ def adjoint(R: fr_routing, w: torch.Tensor, w_lo: Optional[torch.Tensor] = None,
     dev = w.device
     dLdr = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     dLdz = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_dz else None
-    ws = workspace(nx, ny, dev)
+    ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
     check(load().fr_route_adjoint(ctypes.byref(R), _p(w), _p(w_lo), _p(dLdw), _p(dLdr), _p(dLdz),
                                   _p(ws), ws.numel(), _stream()), "fr_route_adjoint")
     return dLdr, dLdz

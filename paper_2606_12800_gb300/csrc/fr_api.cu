@@ -23,6 +23,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // The first three regions are zeroed by each engine call (one memset).
 struct Layout {
     size_t cnt, gbits, lo, link, glist, rb, partials, total, zero_bytes;
+    size_t frac, total_mfd;  // MFD only: fractions (32 B/cell) after the common part
 };
 
 Layout layout(int64_t n) {
@@ -44,6 +45,9 @@ Layout layout(int64_t n) {
     L.partials = off;
     off += align256((size_t)kMassBlocks * 3 * 8);
     L.total = off;
+    L.frac = off;
+    off += align256((size_t)n * 8 * sizeof(float));
+    L.total_mfd = off;
     return L;
 }
 
@@ -55,6 +59,11 @@ fr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FR_OK : FR_ERR_
 
 bool ws_ok(const void* ws, size_t ws_bytes, int64_t n) {
     return ws && ((uintptr_t)ws & 255) == 0 && ws_bytes >= layout(n).total;
+}
+
+// MFD operations also keep the fractions of every cell in the workspace.
+bool ws_ok_mfd(const void* ws, size_t ws_bytes, int64_t n) {
+    return ws && ((uintptr_t)ws & 255) == 0 && ws_bytes >= layout(n).total_mfd;
 }
 
 // FR_CHECK_FINITE uses a counter in the library's own device memory (module
@@ -82,7 +91,7 @@ bool routing_ok(const fr_routing* R) {
     if (R->kind == FR_ROUTING_D8) return R->dir != nullptr;
     if (R->kind == FR_ROUTING_MFD)
         return R->mask && R->dem && std::isfinite(R->dx) && R->dx > 0 && std::isfinite(R->p) &&
-               R->p > 0 && (R->flags & ~kKnownFlags) == 0;
+               R->p > 0 && R->p <= FR_MFD_MAX_P && (R->flags & ~kKnownFlags) == 0;
     return false;
 }
 
@@ -100,6 +109,7 @@ Prob base_prob(const fr_routing* R, char* ws) {
     P.glist = reinterpret_cast<unsigned long long*>(ws + L.glist);
     P.glist_cap = R->nx * R->ny;
     P.out_lo = reinterpret_cast<float*>(ws + L.lo);
+    if (R->kind == FR_ROUTING_MFD) P.frac = reinterpret_cast<const float*>(ws + L.frac);
     P.mc = make_mfd_const(R->kind == FR_ROUTING_MFD ? R->dx : 1.0, R->kind == FR_ROUTING_MFD ? R->p : 1.0);
     return P;
 }
@@ -129,6 +139,7 @@ int32_t fr_version(void) { return 100; }
 size_t fr_workspace_size(int32_t op, int64_t nx, int64_t ny, uint32_t flags) {
     if (!sizes_ok(nx, ny) || (flags & ~kKnownFlags)) return 0;
     if (op == FR_OP_RECEIVERS) return 0;
+    if (op == FR_OP_MFD) return layout(nx * ny).total_mfd;
     if (op < 0 || op > FR_OP_ROUTE) return 0;
     return layout(nx * ny).total;
 }
@@ -166,7 +177,7 @@ fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, 
                            uint32_t flags, uint8_t* mask_out, float* frac_out, uint8_t* indeg_out,
                            void* stream) {
     if (!dem || !mask_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
-        !std::isfinite(p) || p <= 0 || (flags & ~kKnownFlags))
+        !std::isfinite(p) || p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags))
         return FR_ERR_INVALID_ARG;
     if (frac_out && ((uintptr_t)frac_out & 15)) return FR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -178,15 +189,23 @@ fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, 
                                             indeg_out, s));
 }
 
-fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, float* w_lo_out,
-                        uint64_t* area_out, void* ws, size_t ws_bytes, void* stream) {
+}  // extern "C"
+
+namespace fr {
+namespace {
+
+// fr_accumulate; fracs_ready: the MFD fractions are already in the workspace
+// (fr_route_mfd computes them together with the masks).
+fr_status accumulate_impl(const fr_routing* R, const float* rain, float* w_out, float* w_lo_out,
+                          uint64_t* area_out, void* ws, size_t ws_bytes, cudaStream_t s,
+                          bool fracs_ready) {
     if (!routing_ok(R)) return FR_ERR_INVALID_ARG;
     if (!w_out && !w_lo_out && !area_out) return FR_ERR_INVALID_ARG;
     if (w_lo_out && !w_out) return FR_ERR_INVALID_ARG;
-    if (R->kind == FR_ROUTING_MFD && (area_out || !w_out)) return FR_ERR_INVALID_ARG;
+    const bool mfd = R->kind == FR_ROUTING_MFD;
+    if (mfd && (area_out || !w_out)) return FR_ERR_INVALID_ARG;
     const int64_t n = R->nx * R->ny;
-    if (!ws_ok(ws, ws_bytes, n)) return FR_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
+    if (!(mfd ? ws_ok_mfd(ws, ws_bytes, n) : ws_ok(ws, ws_bytes, n))) return FR_ERR_WORKSPACE;
     Prob P = base_prob(R, (char*)ws);
     P.init = rain;
     P.out_hi = w_out;
@@ -199,9 +218,24 @@ fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, fl
     cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, s);
     if (e != cudaSuccess) return FR_ERR_CUDA;
     EngineGlobals* G = reinterpret_cast<EngineGlobals*>(ws);
-    if (R->kind == FR_ROUTING_D8)
-        return cuda_status(launch_d8_forward(w_out != nullptr, area_out != nullptr, P, G, s));
+    if (!mfd) return cuda_status(launch_d8_forward(w_out != nullptr, area_out != nullptr, P, G, s));
+    if (!fracs_ready) {
+        e = launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p,
+                                 reinterpret_cast<float*>((char*)ws + L.frac), s);
+        if (e != cudaSuccess) return FR_ERR_CUDA;
+    }
     return cuda_status(launch_mfd_forward(P, G, s));
+}
+
+}  // namespace
+}  // namespace fr
+
+extern "C" {
+
+fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, float* w_lo_out,
+                        uint64_t* area_out, void* ws, size_t ws_bytes, void* stream) {
+    return accumulate_impl(R, rain, w_out, w_lo_out, area_out, ws, ws_bytes, (cudaStream_t)stream,
+                           false);
 }
 
 fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
@@ -228,11 +262,14 @@ fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, doub
                        uint32_t flags, const float* rain, float* w_out, float* w_lo_out,
                        uint8_t* mask_out, void* ws, size_t ws_bytes, void* stream) {
     if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || !std::isfinite(p) ||
-        p <= 0 || (flags & ~kKnownFlags))
+        p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags))
         return FR_ERR_INVALID_ARG;
-    if (!ws_ok(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
-    uint8_t* mask = mask_out ? mask_out : reinterpret_cast<uint8_t*>((char*)ws + layout(nx * ny).rb);
-    fr_status st = fr_receivers_mfd(dem, nx, ny, dx, p, flags, mask, nullptr, nullptr, stream);
+    if (!ws_ok_mfd(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
+    const Layout L = layout(nx * ny);
+    uint8_t* mask = mask_out ? mask_out : reinterpret_cast<uint8_t*>((char*)ws + L.rb);
+    // masks and fractions in one pass
+    fr_status st = fr_receivers_mfd(dem, nx, ny, dx, p, flags, mask,
+                                    reinterpret_cast<float*>((char*)ws + L.frac), nullptr, stream);
     if (st != FR_OK) return st;
     fr_routing R;
     std::memset(&R, 0, sizeof(R));
@@ -244,7 +281,8 @@ fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, doub
     R.dx = dx;
     R.p = p;
     R.flags = flags & ~FR_CHECK_FINITE;
-    return fr_accumulate(&R, rain, w_out, w_lo_out, nullptr, ws, ws_bytes, stream);
+    return accumulate_impl(&R, rain, w_out, w_lo_out, nullptr, ws, ws_bytes, (cudaStream_t)stream,
+                           true);
 }
 
 fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_lo,
@@ -253,7 +291,8 @@ fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_l
     if (!routing_ok(R) || !w || !dLdr_out) return FR_ERR_INVALID_ARG;
     if (dLdz_out && R->kind != FR_ROUTING_MFD) return FR_ERR_INVALID_ARG;
     const int64_t n = R->nx * R->ny;
-    if (!ws_ok(ws, ws_bytes, n)) return FR_ERR_WORKSPACE;
+    const bool mfd = R->kind == FR_ROUTING_MFD;
+    if (!(mfd ? ws_ok_mfd(ws, ws_bytes, n) : ws_ok(ws, ws_bytes, n))) return FR_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     Prob P = base_prob(R, (char*)ws);
     P.init = dLdw;
@@ -263,7 +302,10 @@ fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_l
     P.lo_full = dLdz_out ? 1 : 0;  // the elevation gradient reads every trailing word
     const Layout L = layout(n);
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return FR_ERR_CUDA;
-    cudaError_t e = launch_adjoint(R->kind == FR_ROUTING_MFD, P, reinterpret_cast<EngineGlobals*>(ws), s);
+    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p,
+                                    reinterpret_cast<float*>((char*)ws + L.frac), s) != cudaSuccess)
+        return FR_ERR_CUDA;
+    cudaError_t e = launch_adjoint(mfd, P, reinterpret_cast<EngineGlobals*>(ws), s);
     if (e != cudaSuccess) return FR_ERR_CUDA;
     if (dLdz_out) {
         e = launch_mfd_grad_z(P, dLdr_out, P.out_lo, dLdz_out, s);

@@ -18,7 +18,7 @@ namespace {
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct BatchLayout {
-    size_t cnt, gbits, zero_bytes, lo, link, glist, probs, pre_recv, pre_eng, total;
+    size_t cnt, gbits, zero_bytes, lo, link, glist, probs, pre_recv, pre_eng, frac, total;
     int64_t cells, eng_tiles;
 };
 
@@ -52,6 +52,8 @@ BatchLayout batch_layout(const fr_tile* t, int n, int kind = FR_ROUTING_D8, int 
     off += a256((size_t)(n + 1) * 8);
     L.pre_eng = off;
     off += a256((size_t)(n + 1) * 8);
+    L.frac = off;  // MFD: fractions of every cell of every tile
+    if (kind == FR_ROUTING_MFD) off += a256((size_t)cells * 8 * sizeof(float));
     L.total = off;
     L.cells = cells;
     L.eng_tiles = et;
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restr
         P.cnt = reinterpret_cast<uint32_t*>(ws + L.cnt + o_cb);
         P.gbits = reinterpret_cast<uint32_t*>(ws + L.gbits) + o_gw;
         P.link = reinterpret_cast<int64_t*>(ws + L.link) + o_cells;
+        if (kind == FR_ROUTING_MFD) P.frac = reinterpret_cast<const float*>(ws + L.frac) + 8 * o_cells;
         P.glist = reinterpret_cast<unsigned long long*>(ws + L.glist);
         P.glist_cap = L.cells;
         P.mc = make_mfd_const(t.dx, kind == FR_ROUTING_MFD ? p : 1.0);
@@ -218,7 +221,7 @@ extern "C" {
 size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_t kind,
                                uint32_t flags) {
     if (!tiles_ok(tiles_host, ntiles, kind) || (flags & ~(FR_EDGE_ROUTE | FR_D8_LOWEST))) return 0;
-    return batch_layout(tiles_host, ntiles).total;
+    return batch_layout(tiles_host, ntiles, kind).total;
 }
 
 fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
@@ -227,8 +230,8 @@ fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, in
     if (kind != FR_ROUTING_D8 && kind != FR_ROUTING_MFD) return FR_ERR_INVALID_ARG;
     if (!tiles_dev || !tiles_ok(tiles_host, ntiles, kind)) return FR_ERR_INVALID_ARG;
     if (flags & ~(FR_EDGE_ROUTE | FR_D8_LOWEST)) return FR_ERR_INVALID_ARG;
-    if (kind == FR_ROUTING_MFD && !(p > 0 && p < 1e30)) return FR_ERR_INVALID_ARG;
-    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < batch_layout(tiles_host, ntiles).total)
+    if (kind == FR_ROUTING_MFD && !(p > 0 && p <= FR_MFD_MAX_P)) return FR_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < batch_layout(tiles_host, ntiles, kind).total)
         return FR_ERR_WORKSPACE;
     Tune t;
     {

@@ -247,6 +247,24 @@ __device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
     return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
 }
 
+// The fractions of a cell with receiver mask m (App. A): f_k = u_k / S with
+// S = sum of u_k over the mask, summed in the pairwise order of df_tree8 and
+// inverted as two-float, each f_k rounded once to fp32; 0 where bit k is clear.
+// Every MFD kernel takes its fractions from this one definition.
+__device__ __forceinline__ void mfd_fracs8(float zc, const float (&zn)[8], uint32_t m,
+                                           const MfdConst& mc, float (&f)[8]) {
+    float u[8];
+    df t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        u[k] = ((m >> k) & 1u) ? mfd_u(zc, zn[k], k, mc) : 0.0f;
+        t[k] = df_make(u[k]);
+    }
+    const df inv = m ? df_recip(df_tree8(t)) : df_make(0.0f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = ((m >> k) & 1u) ? mfd_frac(u[k], inv).hi : 0.0f;
+}
+
 // ------------------------------------------------------------ byte counters
 // Four 8-bit counters per 32-bit word; atomics add n << 8*(i & 3).  Counts
 // never exceed 8, so no carry crosses into a neighbouring byte.
@@ -254,6 +272,16 @@ __device__ __forceinline__ uint32_t counter_add(uint32_t* words, int64_t i, uint
     uint32_t sh = 8u * (uint32_t)(i & 3);
     uint32_t old = atomicAdd(words + (i >> 2), n << sh);
     return ((old >> sh) & 0xFFu) + n;
+}
+
+// Neighbour codes of cell (x, y) that lie inside the grid.
+__device__ __forceinline__ uint32_t grid_mask8(int64_t x, int64_t y, int64_t nx, int64_t ny) {
+    uint32_t m = 0xFFu;
+    if (x == 0) m &= ~0x64u;       // W NW SW
+    if (x == nx - 1) m &= ~0x91u;  // E NE SE
+    if (y == 0) m &= ~0x32u;       // N NE NW
+    if (y == ny - 1) m &= ~0xC8u;  // S SW SE
+    return m;
 }
 
 __device__ __forceinline__ bool is_edge(int64_t x, int64_t y, int64_t nx, int64_t ny) {

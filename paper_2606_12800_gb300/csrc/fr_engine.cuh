@@ -59,13 +59,7 @@ __device__ __forceinline__ uint32_t recv_mask(uint8_t rb) {
 // always masked with it, so routing bytes that point outside the grid (possible
 // in caller-supplied routings) act as "no receiver" instead of reaching outside.
 __device__ __forceinline__ uint32_t grid_mask(int64_t x, int64_t y, int64_t nx, int64_t ny) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        int64_t xn = x + (int64_t)offx(k), yn = y + (int64_t)offy(k);
-        if (xn >= 0 && yn >= 0 && xn < nx && yn < ny) m |= 1u << k;
-    }
-    return m;
+    return grid_mask8(x, y, nx, ny);
 }
 
 // ------------------------------------------------------------ global view
@@ -135,22 +129,6 @@ __device__ __forceinline__ uint32_t g_targets(const Prob& P, int64_t i) {
     else return g_recv_own<E>(P, i);
 }
 
-// Inverse normaliser 1/S of cell i's own outflow (MFD), from global memory.
-template <class E>
-__device__ __noinline__ df g_inv_norm(const Prob& P, int64_t i) {
-    const uint32_t m = g_recv_own<E>(P, i);
-    const float zc = rd_z(P, i);
-    // the neighbours' elevations are loaded side by side, then summed in code order
-    float zn[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) zn[k] = ((m >> k) & 1u) ? rd_z(P, i + offi(k, P.nx)) : 0.0f;
-    df t[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        t[k] = ((m >> k) & 1u) ? df_make(mfd_u_call(zc, zn[k], k, P.mc)) : df_make(0.0f);
-    return df_recip(df_tree8(t));
-}
-
 // Initial value of a cell: rain (forward) or gbar (adjoint).
 template <class E>
 __device__ __forceinline__ df init_value(const Prob& P, int64_t i, uint32_t recv) {
@@ -179,26 +157,18 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
     if constexpr (E::kVal) {
         df v = init_value<E>(P, t, recv);
         if constexpr (E::kAdj) {
-            df inv;
-            float zc = 0.0f;
-            if constexpr (E::kMfd) {
-                inv = g_inv_norm<E>(P, t);
-                zc = rd_z(P, t);
-            }
             // receiver terms in the fixed pairwise order of df_tree8
             df term[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 term[k] = df_make(0.0f);
                 if (!((recv >> k) & 1u)) continue;
-                const int64_t j = t + offi(k, P.nx);
-                const df gj = g_value<E>(P, j);
-                if constexpr (E::kMfd) term[k] = df_mul(mfd_frac(mfd_u_call(zc, rd_z(P, j), k, P.mc), inv), gj);
+                const df gj = g_value<E>(P, t + offi(k, P.nx));
+                if constexpr (E::kMfd) term[k] = mfd_frac(__ldg(P.frac + t * 8 + k), gj);
                 else term[k] = gj;
             }
             v = df_add(v, df_tree8(term));
         } else {
-            float zc = E::kMfd ? rd_z(P, t) : 0.0f;
             // routing bytes of the eight neighbours, loaded side by side
             const uint32_t gm = grid_mask(x, y, P.nx, P.ny);
             uint32_t dmask = 0;
@@ -213,8 +183,7 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
                     term[k] = df_make(0.0f);
                     if (!((dmask >> k) & 1u)) continue;
                     const int64_t j = t + offi(k, P.nx);
-                    const df wj = g_value<E>(P, j);
-                    term[k] = df_mul(mfd_frac(mfd_u_call(rd_z(P, j), zc, opp(k), P.mc), g_inv_norm<E>(P, j)), wj);
+                    term[k] = mfd_frac(__ldg(P.frac + j * 8 + opp(k)), g_value<E>(P, j));
                 }
                 v = df_add(v, df_tree8(term));
             } else {

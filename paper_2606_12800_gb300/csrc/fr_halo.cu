@@ -17,17 +17,16 @@
 // is its own gbar plus the fraction-weighted adjoints of its receivers; f = 1
 // for D8).  A forward cell waits for its donors and then notifies its
 // receivers; an adjoint cell waits for its receivers and notifies its donors.
-// Fractions are f_{j->k} = u_{j->k} / S_j with u = s^p and S_j the sum of
-// cell j's weights: the kernel keeps each cell's 1/S as two-float and
-// recomputes u from the two elevations.  The eight direction terms of a
-// cell are summed in the fixed pairwise order of df_tree8, exactly as the
-// global phase does, so a cell's value does not depend on which kernel
+// Fractions f_{j->k} = u_{j->k} / S_j (u = s^p, S_j the sum of cell j's
+// weights) are computed once per cell by a fully parallel pass (mfd_fracs8)
+// and read here, so the tile solve evaluates no powers.  The eight direction
+// terms of a cell are summed in the fixed pairwise order of df_tree8, exactly
+// as the global phase does, so a cell's value does not depend on which kernel
 // computed it.
 //
 // Cells are finalised level by level from compact lists (a topological order,
-// Sec. 3.2).  Eight lanes serve one cell, one per direction (terms, target
-// updates), so a level of a few dozen cells still keeps the warps busy and
-// its critical path is one weight, not eight.
+// Sec. 3.2).  One thread finalises one cell of a level: its (up to eight)
+// dependency terms are loaded side by side and summed in the fixed order.
 #include "fr_engine.cuh"
 
 namespace fr {
@@ -35,7 +34,6 @@ namespace {
 
 constexpr int kHaloTX = kMfdTileX, kHaloTY = kMfdTileY, kHaloH = 8;
 constexpr int kHaloNT = 512;
-constexpr int NG = kHaloNT / 8;  // cells served at once (eight lanes each)
 
 struct HaloGeo {
     static constexpr int TX = kHaloTX, TY = kHaloTY, H = kHaloH;
@@ -43,7 +41,6 @@ struct HaloGeo {
     static constexpr int RX = EX + 2, RY = EY + 2, NR = RX * RY;         // plus a one-cell ring
     static_assert(NE < 65535, "local indices are 16-bit");
     static_assert(NE % 4 == 0, "state bytes are packed four to a word");
-    static_assert(NE % NG == 0, "whole passes of eight-lane groups");
 };
 
 // Directions whose neighbour of region cell (ex, ey) lies inside the region.
@@ -66,9 +63,6 @@ struct SmemHalo {
     static constexpr int NE = HaloGeo::NE, NR = HaloGeo::NR;
     float vhi[NE];        // value (water or adjoint), leading word
     float vlo[NE];        // value, trailing word
-    float ihi[NE];        // 1/S, leading word (MFD; 0 for a cell without receivers)
-    float ilo[NE];        // 1/S, trailing word
-    float z[NR];          // elevations of region + ring (MFD; +inf outside the grid)
     uint32_t st[NE / 4];  // per cell byte: pending non-bare dependencies (bits 0-3), kG
     uint16_t queue[NE];   // level lists, appended one after another
     uint8_t rb[NR];       // receiver masks of region + ring (0 outside the grid)
@@ -119,7 +113,7 @@ __device__ __forceinline__ int batch_problem_halo(const int64_t* __restrict__ pr
 }
 
 template <Mode M, bool BATCH>
-__global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlobals* G,
+__global__ void __launch_bounds__(kHaloNT, 3) k_local_halo(Prob Pone, EngineGlobals* G,
                                                            const Prob* __restrict__ probs,
                                                            const int64_t* __restrict__ prefix,
                                                            int nprob) {
@@ -141,30 +135,44 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
     const int64_t ox = x0 - H - 1, oy = y0 - H - 1;  // ring origin (may be negative)
     if (tid == 0) S.qtail = 0;
 
-    // ---- region + ring: receiver masks (and elevations for MFD)
+    // ---- region + ring: receiver masks
     for (int i = tid; i < NR; i += NT) {
         const int ry = i / RX, rx = i - ry * RX;
         const int64_t gx = ox + rx, gy = oy + ry;
-        float z = __int_as_float(0x7f800000);
         uint8_t m = 0;
-        if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
-            const int64_t g = gy * P.nx + gx;
-            if constexpr (HM::kMfd) z = rd_z(P, g);
-            m = (uint8_t)(recv_mask<HM::kMfd>(rd_rb(P, g)) & grid_mask(gx, gy, P.nx, P.ny));
-        }
-        if constexpr (HM::kMfd) S.z[i] = z;
+        if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny)
+            m = (uint8_t)(recv_mask<HM::kMfd>(rd_rb(P, gy * P.nx + gx)) & grid_mask(gx, gy, P.nx, P.ny));
         S.rb[i] = m;
+    }
+    if constexpr (HM::kMfd) {
+        // warm L2 with the region's fractions, which the level pulls read a few
+        // at a time: one prefetch per 128-byte line of every region row
+        constexpr int EY = HaloGeo::EY;
+        const int64_t gx0 = ox + 1 < 0 ? 0 : ox + 1;
+        const int64_t gx1 = ox + 1 + EX > P.nx ? P.nx : ox + 1 + EX;
+        if (gx1 > gx0) {
+            const int lines = (int)(((gx1 - gx0) * 32 + 127) / 128) + 1;
+            for (int i = tid; i < EY * lines; i += NT) {
+                const int ry = i / lines, q = i - ry * lines;
+                const int64_t gy = oy + 1 + ry;
+                if (gy < 0 || gy >= P.ny) continue;
+                const char* row = reinterpret_cast<const char*>(P.frac + (gy * P.nx + gx0) * 8);
+                const char* a = row + 128 * q;
+                if (a < reinterpret_cast<const char*>(P.frac + (gy * P.nx + gx1) * 8))
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
+        }
     }
     __syncthreads();
 
     // ---- per region cell: dependencies and targets, bare / global flags,
-    // 1/S (MFD), initial value (rain forward; gbar adjoint)
+    // initial value (rain forward; gbar adjoint)
     for (int c = tid; c < NE; c += NT) {
         const int ey = c / EX, ex = c - ey * EX;
         const int r = (ey + 1) * RX + ex + 1;
         const int64_t gx = ox + ex + 1, gy = oy + ey + 1;
         uint8_t dmr = 0, tmr = 0, fin = 0x0F, b = 0;
-        float ih = 0.0f, il = 0.0f, vh = 0.0f, vl = 0.0f;
+        float vh = 0.0f, vl = 0.0f;
         if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
             const int64_t gi = gy * P.nx + gx;
             uint32_t don = 0;
@@ -179,21 +187,6 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
             tmr = (uint8_t)(tgt & in);
             b = (dep & ~in) ? (uint8_t)kG : (uint8_t)0;
             fin = dep == 0;
-            if constexpr (HM::kMfd) {
-                if (rcv) {
-                    // the eight weights are independent: evaluate them side by side
-                    const float zc = S.z[r];
-                    df t[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        t[k] = ((rcv >> k) & 1u)
-                                   ? df_make(mfd_u(zc, S.z[r + offy(k) * RX + offx(k)], k, P.mc))
-                                   : df_make(0.0f);
-                    const df inv = df_recip(df_tree8(t));
-                    ih = inv.hi;
-                    il = inv.lo;
-                }
-            }
             if constexpr (!HM::kAdj) {
                 vh = P.init ? rd_in(P.init, P, gi, 8) : 1.0f;
             } else if (P.init) {
@@ -208,8 +201,6 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
         S.tm[c] = tmr;
         S.fin[c] = fin;
         stb[c] = b;
-        S.ihi[c] = ih;
-        S.ilo[c] = il;
         S.vhi[c] = vh;
         S.vlo[c] = vl;
     }
@@ -232,55 +223,67 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
     }
     __syncthreads();
 
-    // Below, eight lanes serve one cell: lane k8 looks at direction k8.
-    const int k8 = tid & 7;
-    const int grp = tid >> 3;
-
     // ---- levels: finalise each level's list, collect the next one
     {
         int lo = 0, hi = S.qtail;
         while (lo < hi) {
-            for (int base = lo; base < hi; base += NG) {
-                const int i = base + grp;
-                const bool valid = i < hi;
-                const int c = valid ? (int)S.queue[i] : 0;
-                const bool glob = valid && (st_byte(S.st, c) & kG);
-                const int ey = c / EX, ex = c - ey * EX;
-                const int r = (ey + 1) * RX + ex + 1;
-                // lane k8 takes the dependency in direction k8
-                df term = df_make(0.0f);
-                if (valid && !glob && ((S.dm[c] >> k8) & 1u)) {
-                    const int j = c + offy(k8) * EX + offx(k8);
-                    const df vj = {S.vhi[j], S.vlo[j]};
-                    if constexpr (M == Mode::FwdMfd) {
-                        const float u = mfd_u(S.z[r + offy(k8) * RX + offx(k8)], S.z[r], opp(k8), P.mc);
-                        term = df_mul(mfd_frac(u, df{S.ihi[j], S.ilo[j]}), vj);
-                    } else if constexpr (M == Mode::AdjMfd) {
-                        const float u = mfd_u(S.z[r], S.z[r + offy(k8) * RX + offx(k8)], k8, P.mc);
-                        term = df_mul(mfd_frac(u, df{S.ihi[c], S.ilo[c]}), vj);
-                    } else {
-                        term = vj;
-                    }
-                }
-                const df total = df_tree8_lanes(term);
-                if (valid && k8 == 0) {
+            for (int base = lo; base < hi; base += NT) {
+                const int i = base + tid;
+                int c = 0;
+                uint32_t ready = 0;  // codes of targets whose count reached zero
+                if (i < hi) {
+                    c = S.queue[i];
+                    const bool glob = st_byte(S.st, c) & kG;
                     if (!glob) {
-                        const df v = df_add(df{S.vhi[c], S.vlo[c]}, total);
+                        // dependency terms, loaded side by side, summed in the
+                        // fixed pairwise order of df_tree8
+                        const uint32_t dm = S.dm[c];
+                        int64_t gc = 0;
+                        if constexpr (HM::kMfd) {
+                            const int ey = c / EX, ex = c - ey * EX;
+                            gc = (oy + ey + 1) * P.nx + (ox + ex + 1);
+                        }
+                        df term[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            term[k] = df_make(0.0f);
+                            if (!((dm >> k) & 1u)) continue;
+                            const int j = c + offy(k) * EX + offx(k);
+                            const df vj = {S.vhi[j], S.vlo[j]};
+                            if constexpr (HM::kMfd) {
+                                // forward: the donor's fraction towards c; adjoint:
+                                // c's own fraction towards the receiver
+                                const int64_t fi = HM::kAdj ? gc * 8 + k : (gc + offi(k, P.nx)) * 8 + opp(k);
+                                term[k] = mfd_frac(__ldg(P.frac + fi), vj);
+                            } else {
+                                term[k] = vj;
+                            }
+                        }
+                        const df v = df_add(df{S.vhi[c], S.vlo[c]}, df_tree8(term));
                         S.vhi[c] = v.hi;
                         S.vlo[c] = v.lo;
                     }
                     S.fin[c] = 1;
+                    // targets: pass on the global flag, count down
+                    for (uint32_t m = S.tm[c]; m; m &= m - 1) {
+                        const int k = __ffs(m) - 1;
+                        const int t = c + offy(k) * EX + offx(k);
+                        const uint32_t sh = 8u * (uint32_t)(t & 3);
+                        if (glob) atomicOr(&S.st[t >> 2], kG << sh);
+                        const uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
+                        if (((old >> sh) & 0x0Fu) == 1u) ready |= 1u << k;
+                    }
                 }
-                // targets: lane k8 passes on the global flag and counts down
-                int ready = -1;
-                if (valid && ((S.tm[c] >> k8) & 1u)) {
-                    const int t = c + offy(k8) * EX + offx(k8);
-                    const uint32_t sh = 8u * (uint32_t)(t & 3);
-                    if (glob) atomicOr(&S.st[t >> 2], kG << sh);
-                    const uint32_t old = atomicSub(&S.st[t >> 2], 1u << sh);
-                    if (((old >> sh) & 0x0Fu) == 1u) ready = t;
+                // append the ready targets, one warp-aggregated append per round
+                while (__any_sync(0xffffffffu, ready != 0)) {
+                    int cell = -1;
+                    if (ready) {
+                        const int k = __ffs(ready) - 1;
+                        ready &= ready - 1;
+                        cell = c + offy(k) * EX + offx(k);
+                    }
+                    push_cell(S, cell);
                 }
-                push_cell(S, ready);
             }
             __syncthreads();  // the level's values and the next list are complete
             lo = hi;

@@ -24,7 +24,8 @@ cudaError_t launch_count_nonfinite(const float* z, int64_t n, unsigned long long
 struct Prob {
     int64_t nx, ny;
     const uint8_t* rb;     // routing bytes: D8 codes or MFD masks
-    const float* z;        // MFD elevations (fractions are recomputed)
+    const float* z;        // MFD elevations (receivers of batched tiles)
+    const float* frac;     // MFD fractions [cell * 8 + code], see mfd_fracs8
     const float* init;     // forward: rain (NULL = unit); adjoint: dL/dw (NULL = sink loss)
     const float* wf;       // adjoint: forward water (leading word)
     const float* wf_lo;    // adjoint: forward water (trailing word) or NULL
@@ -86,6 +87,8 @@ cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t*
                                 const float* rain, const float* w, const float* w_lo,
                                 const uint64_t* area, double* partials, int nblocks,
                                 double* out, cudaStream_t s);
+cudaError_t launch_mfd_fractions(const float* z, const uint8_t* mask, int64_t nx, int64_t ny,
+                                 double dx, double p, float* frac, cudaStream_t s);
 cudaError_t launch_receivers_batch(int kind, const Prob* probs, const int64_t* prefix, int nprob,
                                    uint32_t flags, EngineGlobals* G, int grid, cudaStream_t s);
 

@@ -183,26 +183,10 @@ __device__ __forceinline__ void recv_mfd_tile(const float* __restrict__ z, int64
         uint8_t m = ms[(ly + 1) * RX + lx + 1];
         mask[gi] = m;
         if (FRAC) {
-            float zc = zs[(ly + 2) * HX + (lx + 2)];
-            float u[8];
-            df s = df_make(0.0f);
+            float zn[8], f[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                u[k] = 0.0f;
-                if (m & (1u << k)) {
-                    u[k] = mfd_u(zc, zs[(ly + 2 + offy(k)) * HX + (lx + 2 + offx(k))], k, mc);
-                    s = df_add(s, df_make(u[k]));
-                }
-            }
-            float f[8];
-            if (m) {
-                df inv = df_recip(s);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) f[k] = (m & (1u << k)) ? mfd_frac(u[k], inv).hi : 0.0f;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) f[k] = 0.0f;
-            }
+            for (int k = 0; k < 8; ++k) zn[k] = zs[(ly + 2 + offy(k)) * HX + (lx + 2 + offx(k))];
+            mfd_fracs8(zs[(ly + 2) * HX + (lx + 2)], zn, m, mc, f);
             float4* fo = reinterpret_cast<float4*>(frac + gi * 8);
             fo[0] = make_float4(f[0], f[1], f[2], f[3]);
             fo[1] = make_float4(f[4], f[5], f[6], f[7]);
@@ -226,6 +210,34 @@ __global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__
     int64_t x0, y0;
     tile_origin(nx, x0, y0);
     recv_mfd_tile<FRAC, INDEG>(z, nx, ny, mc, flags, mask, frac, indeg, x0, y0);
+}
+
+// Fractions of given receiver masks (bits pointing off the grid are
+// ignored): one cell per thread, elevations staged like the receiver tiles.
+__global__ void __launch_bounds__(RNT) k_mfd_fractions(const float* __restrict__ z,
+                                                       const uint8_t* __restrict__ mask,
+                                                       int64_t nx, int64_t ny, MfdConst mc,
+                                                       float* __restrict__ frac) {
+    __shared__ float zs[HX * HY];
+    int64_t x0, y0;
+    tile_origin(nx, x0, y0);
+    load_z_tile(zs, z, nx, ny, x0, y0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < RTX * RTY; i += RNT) {
+        const int ly = i / RTX, lx = i - ly * RTX;
+        const int64_t gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        const int64_t gi = gy * nx + gx;
+        if (!FR_OK(gi, nx * ny, 43)) continue;
+        const uint32_t m = mask[gi] & grid_mask8(gx, gy, nx, ny);
+        float zn[8], f[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) zn[k] = zs[(ly + 2 + offy(k)) * HX + (lx + 2 + offx(k))];
+        mfd_fracs8(zs[(ly + 2) * HX + (lx + 2)], zn, m, mc, f);
+        float4* fo = reinterpret_cast<float4*>(frac + gi * 8);
+        fo[0] = make_float4(f[0], f[1], f[2], f[3]);
+        fo[1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
 }
 
 // Batched receivers: persistent CTAs claim receiver tiles of any problem.
@@ -259,8 +271,8 @@ __global__ void __launch_bounds__(RNT) k_receivers_batch(int kind, const Prob* _
             recv_d8_tile<false, false>(P.z, P.nx, P.ny, P.mc.co_hi, P.mc.cd_hi, flags,
                                        const_cast<uint8_t*>(P.rb), nullptr, tx * RTX, ty * RTY);
         else
-            recv_mfd_tile<false, false>(P.z, P.nx, P.ny, P.mc, flags, const_cast<uint8_t*>(P.rb),
-                                        nullptr, nullptr, tx * RTX, ty * RTY);
+            recv_mfd_tile<true, false>(P.z, P.nx, P.ny, P.mc, flags, const_cast<uint8_t*>(P.rb),
+                                       const_cast<float*>(P.frac), nullptr, tx * RTX, ty * RTY);
         __syncthreads();
     }
 }
@@ -308,6 +320,13 @@ cudaError_t launch_receivers_mfd(const float* z, int64_t nx, int64_t ny, double 
     else
         k_receivers_mfd<false, false><<<grid, RNT, 0, s>>>(z, nx, ny, mc, flags, mask, nullptr,
                                                            nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mfd_fractions(const float* z, const uint8_t* mask, int64_t nx, int64_t ny,
+                                 double dx, double p, float* frac, cudaStream_t s) {
+    const unsigned grid = (unsigned)(((nx + RTX - 1) / RTX) * ((ny + RTY - 1) / RTY));
+    k_mfd_fractions<<<grid, RNT, 0, s>>>(z, mask, nx, ny, make_mfd_const(dx, p), frac);
     return cudaGetLastError();
 }
 

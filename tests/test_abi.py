@@ -44,6 +44,9 @@ def test_workspace_size(lib):
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 0, 10, 0) == 0
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 10, 10, 0x80) == 0
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 1 << 21, 1 << 21, 0) == 0  # > 2^40 cells
+    # MFD operations keep 8 fp32 fractions per cell on top of the common part
+    m = lib.fr_workspace_size(_lib.FR_OP_MFD, 4096, 4096, 0)
+    assert m >= n + 4096 * 4096 * 32 and m % 256 == 0
 
 
 def test_argument_validation_is_synchronous(lib):
@@ -56,6 +59,9 @@ def test_argument_validation_is_synchronous(lib):
     assert lib.fr_receivers_d8(fake, 4, 4, float("nan"), 0, fake, None, None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_receivers_d8(fake, 4, 4, 1.0, 0x100, fake, None, None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 0.0, 0, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 65.0, 0, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
+    # fractions need 16-byte alignment
+    assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 1.1, 0, fake, P(0x1004), None, None) == _lib.FR_ERR_INVALID_ARG
     R = _lib.fr_routing()
     R.kind = 7
     R.nx = R.ny = 4
@@ -75,6 +81,12 @@ def test_argument_validation_is_synchronous(lib):
     R.dx = 30.0
     R.p = 1.1
     assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+    # an MFD routing needs the larger workspace (fractions)
+    small = lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 4, 4, 0)
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, P(0x10000), small, None) == _lib.FR_ERR_WORKSPACE
+    R.p = 100.0
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, P(0x10000), 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+    R.p = 1.1
     R.kind = _lib.FR_ROUTING_D8
     assert lib.fr_route_adjoint(ctypes.byref(R), fake, None, None, fake, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
     R.reserved = 1
