@@ -396,6 +396,66 @@ def extra_rows(api, L, dev, peak, want):
     return rows
 
 
+def adjoint_row(api, dev, peak, timed):
+    """Slope-split on 16384^2 (beta 2.2, no tilt, unit rain): forward, then the
+    adjoint of L = sum over sinks of w^2 giving dL/drain and dL/dz."""
+    from paper_2606_12800_gb300 import inputs
+    n = 16384
+    zt = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=SEED + 4, device="cuda")
+    m = api.receivers_mfd(zt, DX, 1.1)
+    R = api.routing_mfd(m, zt, DX, 1.1)
+    fwd = api.accumulate(R, None, want_w=True, want_lo=True, device=dev)
+
+    def adj():
+        return api.adjoint(R, fwd["w"], fwd["w_lo"], want_dz=True)
+    ms = timed(adj, reps=3)
+    status = api.get_status(dev)
+    del zt, m, fwd
+    # algorithmic bytes: z 4 + w 8 (two words) in, dL/dr 4 + dL/dz 4 out
+    return {"ms": ms, "value": n * n / (ms * 1e-3), "unit": "cells/s", "status": status,
+            "workload": "MFD p=1.1 adjoint of L = sum over sinks of w^2, %dx%d fractal DEM "
+                        "beta=2.2, dL/drain and dL/dz" % (n, n),
+            "hbm_frac": (n * n * 20) / (ms * 1e-3) / 1e9 / peak}
+
+
+def d8_large_row(api, L, dev, peak, timed):
+    """D8 on 32768^2 (beta 2, tilt 0.005, unit rain): receivers + exact uint64
+    areas; the accumulation alone against the roofline (dir 1 B in, area 8 B
+    out per cell)."""
+    import ctypes
+    import torch
+    from paper_2606_12800_gb300 import _lib, inputs
+    n = 32768
+    P = ctypes.c_void_p
+    zt = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.005, seed=SEED + 5, device="cuda")
+    d = torch.empty((n, n), dtype=torch.uint8, device=dev)
+    area = torch.empty((n, n), dtype=torch.int64, device=dev)
+    ws = api.workspace(n, n, dev)
+    R = api.routing_d8(d)
+
+    def recv():
+        _lib.check(L.fr_receivers_d8(P(zt.data_ptr()), n, n, DX, 0, P(d.data_ptr()), None,
+                                     api._stream()), "fr_receivers_d8")
+
+    def acc():
+        _lib.check(L.fr_accumulate(ctypes.byref(R), None, None, None, P(area.data_ptr()),
+                                   P(ws.data_ptr()), ws.numel(), api._stream()), "fr_accumulate")
+    recv()
+    ms_recv = timed(recv, reps=3)
+    ms_acc = timed(acc, reps=3)
+    status = api.get_status(dev)
+    total = int(area.view(-1)[d.view(-1) == 0xFF].sum().item())
+    cells = n * n
+    del zt, d, area
+    return {"ms_receivers": ms_recv, "ms_accumulate": ms_acc,
+            "value": cells / ((ms_recv + ms_acc) * 1e-3), "unit": "cells/s", "status": status,
+            "sink_area_sum_equals_cells": total == cells,
+            "workload": "D8 %dx%d fractal DEM beta=2 tilt=0.005, unit rain, uint64 areas" % (n, n),
+            "accumulate_roofline": {"bound": "hbm", "algorithmic_bytes_per_cell": 9,
+                                    "achieved_gbs": cells * 9 / (ms_acc * 1e-3) / 1e9, "peak": peak,
+                                    "frac": cells * 9 / (ms_acc * 1e-3) / 1e9 / peak}}
+
+
 def batch_rows(api, L, dev):
     """512 independent tiles (sides log-uniform in [64, 2048], beta in [1.8, 2.4],
     rain U[0,1)): one fr_route_batch call replayed from a CUDA graph, against a

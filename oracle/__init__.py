@@ -94,6 +94,10 @@ def lib():
         L.or_upstream_count.argtypes = [P, I64, I64, I64, P, P]
         L.or_upstream_count.restype = ctypes.c_uint64
         L.or_sink_of.argtypes = [P, I64, I64, I64]
+        L.or_mfd_delta_loss.argtypes = [P, I64, I64, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_uint32, P, P, P, I64, ctypes.c_double,
+                                        ctypes.c_int, P, P]
+        L.or_mfd_delta_loss.restype = ctypes.c_double
         L.or_sink_of.restype = I64
         _lib = L
     return _lib
@@ -221,6 +225,32 @@ def mfd_grad_z(z, dx, p, frac, w, g, flags: int = 0) -> np.ndarray:
                         _p(np.ascontiguousarray(w, np.float64)),
                         _p(np.ascontiguousarray(g, np.float64)), _p(out))
     return out
+
+
+class MfdLossDelta:
+    """Exact change of L = sum over sinks of w^2 when z (mode 0) or the rain
+    (mode 1) of one cell changes, for finite-difference checks of the adjoint
+    (see or_mfd_delta_loss).  Keeps the FP64 routing of one grid."""
+
+    def __init__(self, z, dx, p, mask, frac, w, flags: int = 0):
+        self.z = np.ascontiguousarray(z, dtype=np.float64)
+        self.ny, self.nx = self.z.shape
+        self.dx, self.p, self.flags = float(dx), float(p), int(flags)
+        self.mask = np.ascontiguousarray(mask, np.uint8)
+        self.frac = np.ascontiguousarray(frac, np.float64)
+        self.w = np.ascontiguousarray(w, np.float64)
+        self.dwork = np.zeros(self.z.size, np.float64)
+        self.mark = np.zeros(self.z.size, np.uint8)
+
+    def delta(self, cell: int, delta: float, mode: int) -> float:
+        return float(lib().or_mfd_delta_loss(
+            _p(self.z), self.nx, self.ny, self.dx, self.p, self.flags, _p(self.mask),
+            _p(self.frac), _p(self.w), int(cell), float(delta), int(mode), _p(self.dwork),
+            _p(self.mark)))
+
+    def central(self, cell: int, h: float, mode: int) -> float:
+        """(L(x + h) - L(x - h)) / 2h for x = z[cell] (mode 0) or its rain."""
+        return (self.delta(cell, h, mode) - self.delta(cell, -h, mode)) / (2.0 * h)
 
 
 def mass_balance(w, rain=None, dir_=None, mask=None):

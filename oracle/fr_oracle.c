@@ -384,3 +384,153 @@ int64_t or_sink_of(const uint8_t* dir, int64_t nx, int64_t ny, int64_t cell) {
     }
     return -1;
 }
+
+/* ------------------------------------------------------------------------
+ * Exact change of the loss L = sum over sinks of w^2 when one input of cell m
+ * changes by `delta`, without re-solving the whole grid (for finite-difference
+ * checks of the adjoint on grids too large for repeated full solves).
+ *   mode 0: z[m] += delta.  Only the fractions of m and its eight neighbours
+ *           depend on z[m].  With W' the new weights and w the old water,
+ *           A' w' = r and A w = r give A' (w' - w) = (W' - W) w, so the change
+ *           d = w' - w starts at the receivers of those nine cells and is
+ *           passed on with the new fractions.  Returns NaN if the change
+ *           would alter a receiver mask (the weights are then not smooth).
+ *   mode 1: the rain of m += delta; d starts at m and is passed on with the
+ *           unchanged fractions.
+ * d travels strictly downhill, so cells are finalised in decreasing
+ * (perturbed) elevation from a max-heap; the change of L is accumulated at
+ * the sinks as 2 w d + d^2 (no cancellation against L itself).
+ * dwork [n] (doubles) and mark [n] (bytes) must be zero on entry and are zero
+ * again on return.
+ */
+typedef struct {
+    const double* z;
+    int64_t m;
+    double zm;
+} zview;
+
+static double zv(const zview* v, int64_t i) { return i == v->m ? v->zm : v->z[i]; }
+
+/* max-heap of cell indices ordered by (elevation desc, index asc) */
+static int heap_before(const zview* v, int64_t a, int64_t b) {
+    double za = zv(v, a), zb = zv(v, b);
+    return za > zb || (za == zb && a < b);
+}
+static void heap_push(int64_t* h, int64_t* n, int64_t c, const zview* v) {
+    int64_t i = (*n)++;
+    h[i] = c;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!heap_before(v, h[i], h[p])) break;
+        int64_t t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+static int64_t heap_pop(int64_t* h, int64_t* n, const zview* v) {
+    int64_t top = h[0];
+    h[0] = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, b = i;
+        if (l < *n && heap_before(v, h[l], h[b])) b = l;
+        if (r < *n && heap_before(v, h[r], h[b])) b = r;
+        if (b == i) break;
+        int64_t t = h[i]; h[i] = h[b]; h[b] = t;
+        i = b;
+    }
+    return top;
+}
+
+/* Mask and fractions of one cell (the rule of or_receivers_mfd) under view v. */
+static void mfd_cell(const zview* v, int64_t nx, int64_t ny, double dx, double p, uint32_t flags,
+                     int64_t i, uint8_t* mask, double* f) {
+    int64_t x = i % nx, y = i / nx;
+    double u[8], tot = 0.0;
+    *mask = 0;
+    for (int k = 0; k < 8; ++k) { u[k] = 0.0; f[k] = 0.0; }
+    if (!(flags & OR_EDGE_ROUTE) && is_edge(x, y, nx, ny)) return;
+    double zc = zv(v, i);
+    for (int k = 0; k < 8; ++k) {
+        int64_t xn = x + OFFX[k], yn = y + OFFY[k];
+        if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+        double zn = zv(v, yn * nx + xn);
+        if (!(zn < zc)) continue;
+        double d = (k < 4) ? dx : sqrt(2.0) * dx;
+        u[k] = pow((zc - zn) / d, p);
+        *mask |= (uint8_t)(1u << k);
+    }
+    for (int k = 0; k < 8; ++k) tot += u[k];
+    if (tot > 0.0)
+        for (int k = 0; k < 8; ++k) f[k] = u[k] / tot;
+}
+
+double or_mfd_delta_loss(const double* z, int64_t nx, int64_t ny, double dx, double p,
+                         uint32_t flags, const uint8_t* mask, const double* frac, const double* w,
+                         int64_t m, double delta, int mode, double* dwork, uint8_t* mark) {
+    zview v = {z, m, mode == 0 ? z[m] + delta : z[m]};
+    /* the nine cells whose fractions may change, and their new fractions */
+    int64_t aff[9];
+    double fnew[9][8];
+    int naff = 0;
+    int64_t mx = m % nx, my = m / nx;
+    if (mode == 0) {
+        for (int k = -1; k < 8; ++k) {
+            int64_t xn = mx + (k < 0 ? 0 : OFFX[k]), yn = my + (k < 0 ? 0 : OFFY[k]);
+            if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+            int64_t a = yn * nx + xn;
+            uint8_t mk;
+            mfd_cell(&v, nx, ny, dx, p, flags, a, &mk, fnew[naff]);
+            if (mk != mask[a]) return NAN;
+            aff[naff++] = a;
+        }
+    }
+    int64_t cap = 1024, nheap = 0;
+    int64_t* heap = (int64_t*)malloc((size_t)cap * sizeof(int64_t));
+    if (!heap) return NAN;
+#define OR_ADD(cell, amount)                                                       \
+    do {                                                                           \
+        int64_t c_ = (cell);                                                       \
+        dwork[c_] += (amount);                                                     \
+        if (!mark[c_]) {                                                           \
+            mark[c_] = 1;                                                          \
+            if (nheap == cap) {                                                    \
+                cap *= 2;                                                          \
+                int64_t* nh = (int64_t*)realloc(heap, (size_t)cap * sizeof(int64_t)); \
+                if (!nh) { free(heap); return NAN; }                               \
+                heap = nh;                                                         \
+            }                                                                      \
+            heap_push(heap, &nheap, c_, &v);                                       \
+        }                                                                          \
+    } while (0)
+    if (mode == 0) {
+        for (int q = 0; q < naff; ++q) {
+            int64_t a = aff[q];
+            for (int k = 0; k < 8; ++k) {
+                if (!((mask[a] >> k) & 1u)) continue;
+                double ds = (fnew[q][k] - frac[a * 8 + k]) * w[a];
+                OR_ADD(a + OFFY[k] * nx + OFFX[k], ds);
+            }
+        }
+    } else {
+        OR_ADD(m, delta);
+    }
+    double dL = 0.0;
+    while (nheap > 0) {
+        int64_t c = heap_pop(heap, &nheap, &v);
+        double d = dwork[c];
+        dwork[c] = 0.0;
+        mark[c] = 0;
+        if (mask[c] == 0) {
+            dL += 2.0 * w[c] * d + d * d;
+            continue;
+        }
+        const double* fc = frac + c * 8;
+        for (int q = 0; q < naff; ++q)
+            if (aff[q] == c) fc = fnew[q];
+        for (int k = 0; k < 8; ++k)
+            if ((mask[c] >> k) & 1u) OR_ADD(c + OFFY[k] * nx + OFFX[k], d * fc[k]);
+    }
+#undef OR_ADD
+    free(heap);
+    return dL;
+}

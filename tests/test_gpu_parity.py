@@ -282,6 +282,60 @@ def test_slope_split_full_size_workload(api):
     assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
 
 
+def _adjoint_fd_check(api, zt, count, seed):
+    """dL/dz and dL/drain of the GPU adjoint (L = sum over sinks of w^2, unit
+    rain, MFD p = 1.1) against central finite differences of the FP64 oracle,
+    taken exactly and incrementally (oracle.MfdLossDelta) at `count` random
+    interior cells whose elevation gaps to all neighbours exceed 1 mm."""
+    ny, nx = zt.shape
+    m = api.receivers_mfd(zt, 30.0, 1.1)
+    R = api.routing_mfd(m, zt, 30.0, 1.1)
+    fwd = api.accumulate(R, None, want_w=True, want_lo=True)
+    dLdr, dLdz = api.adjoint(R, fwd["w"], fwd["w_lo"], want_dz=True)
+    assert api.get_status() == 0
+    dLdr, dLdz, z = dLdr.cpu().numpy(), dLdz.cpu().numpy(), zt.cpu().numpy()
+    del m, R, fwd
+    torch.cuda.empty_cache()
+    m_ref, f_ref, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, None)
+    D = oracle.MfdLossDelta(z, 30.0, 1.1, m_ref, f_ref, w_ref)
+    z64 = z.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    got_z, fd_z, got_r, fd_r = [], [], [], []
+    while len(fd_z) < count:
+        y, x = int(rng.integers(1, ny - 1)), int(rng.integers(1, nx - 1))
+        gap = min(abs(z64[y, x] - z64[y + oracle.OFFY[k], x + oracle.OFFX[k]]) for k in range(8))
+        if gap < 1e-3:
+            continue
+        fz = D.central(y * nx + x, 1e-3 * gap, 0)
+        if np.isnan(fz):
+            continue
+        fd_z.append(fz)
+        got_z.append(dLdz[y, x])
+        fd_r.append(D.central(y * nx + x, 1e-3, 1))
+        got_r.append(dLdr[y, x])
+    fd_z, got_z, fd_r, got_r = map(np.asarray, (fd_z, got_z, fd_r, got_r))
+    scale = np.abs(fd_z).max()
+    assert np.all(np.abs(got_z - fd_z) <= 1e-4 * np.abs(fd_z) + 1e-6 * scale), \
+        np.max(np.abs(got_z - fd_z) / np.maximum(np.abs(fd_z), 1e-30))
+    assert np.all(np.abs(got_r - fd_r) <= 1e-4 * np.abs(fd_r)), \
+        np.max(np.abs(got_r - fd_r) / np.abs(fd_r))
+
+
+def test_mfd_adjoint_finite_differences(api):
+    """Adjoint against finite differences on a 1024^2 slope-split DEM."""
+    zt = inputs.fractal_dem_torch(1024, 1024, beta=2.2, tilt=0.0, seed=21, device="cuda")
+    _adjoint_fd_check(api, zt, 64, seed=21)
+
+
+@pytest.mark.slow
+def test_mfd_adjoint_finite_differences_full_size(api):
+    """The 16384^2 slope-split adjoint workload (the benchmark's DEM, loss =
+    sum over sinks of w^2): dL/dz and dL/drain at 64 random cells against
+    central finite differences of the FP64 oracle, to 1e-4 relative."""
+    zt = inputs.fractal_dem_torch(16384, 16384, beta=2.2, tilt=0.0, seed=5, device="cuda")
+    _adjoint_fd_check(api, zt, 64, seed=64)
+
+
 def _batch_specs():
     return [(17, 23, 2.0), (64, 64, 1.8), (31, 200, 2.4), (130, 97, 2.1), (300, 257, 2.0),
             (5, 5, 2.2), (1, 40, 2.0), (90, 1, 2.0), (256, 300, 1.9), (128, 64, 2.3)]

@@ -368,3 +368,57 @@ def test_mfd_grad_z_finite_differences(p):
         if checked == 40:
             break
     assert checked == 40
+
+
+def _dense_loss_mfd(z, rain, p):
+    """L = sum over sinks of w^2 with w from a dense solve of (I - W) w = r
+    (fractions of the pinned receiver rule; no oracle accumulation)."""
+    m, f = oracle.receivers_mfd(z, 30.0, p)
+    A = _dense_A_mfd(f)
+    r = np.ones(z.size) if rain is None else rain.astype(np.float64).ravel()
+    w = np.linalg.solve(A, r).reshape(z.shape)
+    return float((w[m == 0] ** 2).sum())
+
+
+@pytest.mark.parametrize("p", [1.1, 1.7])
+def test_mfd_delta_loss_matches_dense_finite_differences(p):
+    """The incremental loss change (z and rain of one cell) reproduces central
+    differences of dense re-solves, and the rain mode the adjoint dL/dr."""
+    ny, nx = 18, 21
+    z = _dem(ny, nx, 12, beta=2.2, tilt=0.0).astype(np.float64)
+    rain = inputs.rain_field(ny, nx, 12)
+    m, f, w, order = oracle.route_mfd(z, 30.0, p, rain)
+    g = oracle.adjoint(order, w, frac=f)
+    D = oracle.MfdLossDelta(z, 30.0, p, m, f, w)
+    rng = np.random.default_rng(3)
+    checked = 0
+    for cell in rng.permutation(z.size):
+        y, x = divmod(int(cell), nx)
+        gaps = [abs(z[y, x] - z[y + OFFY[k], x + OFFX[k]]) for k in range(8)
+                if 0 <= y + OFFY[k] < ny and 0 <= x + OFFX[k] < nx]
+        h = 1e-4 * min(gaps)
+        if h < 1e-7:
+            continue
+        zp = z.copy(); zp[y, x] += h
+        zm = z.copy(); zm[y, x] -= h
+        dense = (_dense_loss_mfd(zp, rain, p) - _dense_loss_mfd(zm, rain, p)) / (2 * h)
+        assert D.central(int(cell), h, 0) == pytest.approx(dense, rel=1e-6, abs=1e-9 * max(1.0, abs(dense)))
+        # rain: L is quadratic in r, so the central difference is exact
+        assert D.central(int(cell), 1e-3, 1) == pytest.approx(g[y, x], rel=1e-10, abs=1e-12)
+        checked += 1
+        if checked == 12:
+            break
+    assert checked == 12
+    # the scratch arrays come back cleared
+    assert not D.dwork.any() and not D.mark.any()
+
+
+def test_mfd_delta_loss_rejects_mask_changes():
+    """A step that reorders two elevations changes a lower set: NaN."""
+    ny, nx = 9, 9
+    z = _dem(ny, nx, 5, beta=2.2, tilt=0.0).astype(np.float64)
+    m, f, w, _ = oracle.route_mfd(z, 30.0, 1.1, None)
+    D = oracle.MfdLossDelta(z, 30.0, 1.1, m, f, w)
+    c = 4 * nx + 4
+    gap = min(abs(z[4, 4] - z[4 + OFFY[k], 4 + OFFX[k]]) for k in range(8))
+    assert np.isnan(D.delta(c, 2.0 * gap + 1.0, 0)) or np.isnan(D.delta(c, -(2.0 * gap + 1.0), 0))
