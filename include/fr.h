@@ -70,6 +70,9 @@ typedef enum {
  *   FR_D8_LOWEST   maximise fl32(z_c - z_k).
  * Both consider only strictly lower neighbours (flats are sinks) and break
  * ties with strict '>' in scan order (the first code wins).
+ *   FR_D4          D8 routing only (rejected for MFD): consider the four
+ *                  orthogonal neighbours E N W S alone, the D4 scheme that
+ *                  Sec. 2.1 names beside D8.
  *   FR_CHECK_FINITE reject a DEM holding NaN or Inf (FR_ERR_NONFINITE; this
  *                  check synchronises the stream).
  */
@@ -78,6 +81,7 @@ typedef enum {
 #define FR_D8_STEEPEST 0x0u
 #define FR_D8_LOWEST 0x2u
 #define FR_CHECK_FINITE 0x4u
+#define FR_D4 0x8u
 
 #define FR_SINK 0xFFu
 
@@ -103,7 +107,7 @@ typedef enum {
  *   dem       [ny*nx] float32 elevations (metres).
  *   nx, ny    grid size, both >= 1, nx*ny < 2^40.
  *   dx        grid spacing (> 0, finite); only the slope rule depends on it.
- *   flags     FR_EDGE_*, FR_D8_*, FR_CHECK_FINITE.
+ *   flags     FR_EDGE_*, FR_D8_*, FR_D4, FR_CHECK_FINITE.
  *   dir_out   [ny*nx] uint8: receiver code 0..7 or FR_SINK.
  *   indeg_out [ny*nx] uint8 or NULL: number of donors of each cell (0..8).
  * Results are bit-identical to the rule stated above.

@@ -52,6 +52,7 @@
 #define OR_SINK 0xFFu
 #define OR_EDGE_ROUTE 1u
 #define OR_D8_LOWEST 2u
+#define OR_D4 8u
 
 static const int OFFX[8] = {+1, 0, -1, 0, +1, -1, -1, +1};
 static const int OFFY[8] = {0, -1, 0, +1, -1, -1, +1, +1};
@@ -61,7 +62,9 @@ static int is_edge(int64_t x, int64_t y, int64_t nx, int64_t ny) {
 }
 
 /* Local flow routing, D8 (Sec. 2.1: the neighbour that is lower and to which
- * the downhill gradient is steepest; footnote: none at the boundary). */
+ * the downhill gradient is steepest; footnote: none at the boundary).  With
+ * OR_D4 only the four orthogonal neighbours are candidates (the D4 scheme
+ * Sec. 2.1 names beside D8). */
 void or_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx, uint32_t flags,
                      uint8_t* dir) {
     float c_orth = (float)(1.0 / dx);
@@ -73,7 +76,8 @@ void or_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx, uint32_t
             if (!(flags & OR_EDGE_ROUTE) && is_edge(x, y, nx, ny)) continue;
             float zc = z[i];
             float best = -1.0f;
-            for (int k = 0; k < 8; ++k) {
+            const int ncand = (flags & OR_D4) ? 4 : 8;
+            for (int k = 0; k < ncand; ++k) {
                 int64_t xn = x + OFFX[k], yn = y + OFFY[k];
                 if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
                 float zn = z[yn * nx + xn];

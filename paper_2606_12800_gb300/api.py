@@ -131,6 +131,16 @@ def _to_cuda(t):
     return t.to("cuda", non_blocking=True), True
 
 
+def _to_host(out: Dict[str, torch.Tensor]) -> Dict[str, torch.Tensor]:
+    """Device results into page-locked host tensors (torch's caching host
+    allocator), copied asynchronously, then one synchronisation."""
+    res = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    for k, v in out.items():
+        res[k].copy_(v, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return res
+
+
 def route_d8(dem: torch.Tensor, dx: float = 30.0, rain: Optional[torch.Tensor] = None,
              flags: int = 0, want_w: bool = True, want_lo: bool = False, want_area: bool = True,
              want_dir: bool = False) -> Dict[str, torch.Tensor]:
@@ -151,7 +161,7 @@ def route_d8(dem: torch.Tensor, dx: float = 30.0, rain: Optional[torch.Tensor] =
                              _p(ws), ws.numel(), _stream()), "fr_route_d8")
     out = {k: v for k, v in (("w", w), ("w_lo", lo), ("area", a), ("dir", d)) if v is not None}
     if host:
-        out = {k: v.to("cpu") for k, v in out.items()}
+        out = _to_host(out)
     return out
 
 
@@ -172,7 +182,7 @@ def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
                               _p(ws), ws.numel(), _stream()), "fr_route_mfd")
     out = {k: v for k, v in (("w", w), ("w_lo", lo), ("mask", m)) if v is not None}
     if host:
-        out = {k: v.to("cpu") for k, v in out.items()}
+        out = _to_host(out)
     return out
 
 

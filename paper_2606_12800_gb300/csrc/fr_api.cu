@@ -12,7 +12,7 @@ namespace {
 
 constexpr int64_t kMaxCells = (int64_t)1 << 40;
 constexpr int kMassBlocks = 1024;
-constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE;
+constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE | FR_D4;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -91,7 +91,8 @@ bool routing_ok(const fr_routing* R) {
     if (R->kind == FR_ROUTING_D8) return R->dir != nullptr;
     if (R->kind == FR_ROUTING_MFD)
         return R->mask && R->dem && std::isfinite(R->dx) && R->dx > 0 && std::isfinite(R->p) &&
-               R->p > 0 && R->p <= FR_MFD_MAX_P && (R->flags & ~kKnownFlags) == 0;
+               R->p > 0 && R->p <= FR_MFD_MAX_P && (R->flags & ~kKnownFlags) == 0 &&
+               !(R->flags & FR_D4);
     return false;
 }
 
@@ -177,7 +178,8 @@ fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, 
                            uint32_t flags, uint8_t* mask_out, float* frac_out, uint8_t* indeg_out,
                            void* stream) {
     if (!dem || !mask_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
-        !std::isfinite(p) || p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags))
+        !std::isfinite(p) || p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags) ||
+        (flags & FR_D4))
         return FR_ERR_INVALID_ARG;
     if (frac_out && ((uintptr_t)frac_out & 15)) return FR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -262,7 +264,7 @@ fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, doub
                        uint32_t flags, const float* rain, float* w_out, float* w_lo_out,
                        uint8_t* mask_out, void* ws, size_t ws_bytes, void* stream) {
     if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || !std::isfinite(p) ||
-        p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags))
+        p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags) || (flags & FR_D4))
         return FR_ERR_INVALID_ARG;
     if (!ws_ok_mfd(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
     const Layout L = layout(nx * ny);

@@ -16,6 +16,7 @@ namespace fr {
 constexpr uint8_t kSink = 0xFF;
 constexpr uint32_t kEdgeRoute = 0x1u;
 constexpr uint32_t kD8Lowest = 0x2u;
+constexpr uint32_t kD4 = 0x8u;
 
 // Offsets as 2-bit fields (offset + 1) packed per code, decoded with plain
 // signed integer arithmetic (a nested-ternary form of these functions was

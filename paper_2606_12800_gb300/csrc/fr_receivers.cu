@@ -59,6 +59,8 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
     __shared__ uint8_t ds[RX * RY];
     const bool lowest = LOWEST;
     const bool edge_route = flags & kEdgeRoute;
+    const bool d4 = flags & kD4;
+    const float inf = __int_as_float(0x7f800000);
     const bool interior = x0 >= 2 && y0 >= 2 && x0 + RTX + 2 <= nx && y0 + RTY + 2 <= ny;
     if (interior) {
         // row by row: a warp per row, lanes along it
@@ -84,8 +86,10 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
         uint32_t packed = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            // D4: the diagonals read +inf, which is never strictly lower
             const float zn[8] = {w[1][q + 2], w[0][q + 1], w[1][q], w[2][q + 1],
-                                 w[0][q + 2], w[0][q], w[2][q], w[2][q + 2]};
+                                 d4 ? inf : w[0][q + 2], d4 ? inf : w[0][q],
+                                 d4 ? inf : w[2][q], d4 ? inf : w[2][q + 2]};
             uint8_t code = (uint8_t)d8_code_sel<LOWEST>(w[1][q + 1], zn, c_orth, c_diag);
             if (!interior) {  // interior tiles hold no edge cell and no cell off the grid
                 const int64_t gx = x0 + qx + q, gy = y0 + r;
@@ -120,6 +124,7 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
                 (edge_route || !is_edge(gx, gy, nx, ny))) {
                 float zn[8];
                 gather8(zs, rx, ry, zn);
+                if (d4) zn[4] = zn[5] = zn[6] = zn[7] = inf;
                 code = d8_code(zs[(ry + 1) * HX + (rx + 1)], zn, c_orth, c_diag, lowest);
             }
             ds[ry * RX + rx] = code;

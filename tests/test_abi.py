@@ -60,6 +60,9 @@ def test_argument_validation_is_synchronous(lib):
     assert lib.fr_receivers_d8(fake, 4, 4, 1.0, 0x100, fake, None, None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 0.0, 0, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 65.0, 0, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
+    # D4 is a D8-only rule
+    assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 1.1, _lib.FR_D4, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_workspace_size(_lib.FR_OP_ROUTE, 4, 4, _lib.FR_D4) > 0
     # fractions need 16-byte alignment
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 1.1, 0, fake, P(0x1004), None, None) == _lib.FR_ERR_INVALID_ARG
     R = _lib.fr_routing()

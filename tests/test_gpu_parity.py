@@ -41,7 +41,8 @@ SHAPES = [(1, 1), (1, 7), (9, 1), (3, 3), (33, 65), (64, 32), (65, 33), (97, 131
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE, oracle.D8_LOWEST,
-                                   oracle.EDGE_ROUTE | oracle.D8_LOWEST])
+                                   oracle.EDGE_ROUTE | oracle.D8_LOWEST, oracle.D4,
+                                   oracle.D4 | oracle.EDGE_ROUTE | oracle.D8_LOWEST])
 def test_receivers_d8_bit_exact(api, shape, flags):
     ny, nx = shape
     z = inputs.fractal_dem(ny, nx, seed=ny * 7 + nx)
@@ -52,7 +53,7 @@ def test_receivers_d8_bit_exact(api, shape, flags):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE])
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE, oracle.D4 | oracle.EDGE_ROUTE])
 def test_route_d8_parity(api, shape, flags):
     ny, nx = shape
     z = inputs.fractal_dem(ny, nx, seed=ny * 3 + nx)

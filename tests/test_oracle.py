@@ -422,3 +422,44 @@ def test_mfd_delta_loss_rejects_mask_changes():
     c = 4 * nx + 4
     gap = min(abs(z[4, 4] - z[4 + OFFY[k], 4 + OFFX[k]]) for k in range(8))
     assert np.isnan(D.delta(c, 2.0 * gap + 1.0, 0)) or np.isnan(D.delta(c, -(2.0 * gap + 1.0), 0))
+
+
+# ------------------------------------------------------------------- D4 ----
+
+def test_d4_plane_closed_form():
+    """z = 10000 - 2x - y (dx = 1): D8's steepest interior receiver is SE
+    (slope 3/sqrt2 > 2), D4's is E; with edge routing the last column of D4
+    routes S, so areas are x + 1 along the rows and nx (y + 1) down the last
+    column, ending in the corner sink with all nx*ny cells."""
+    ny, nx = 7, 9
+    y, x = np.mgrid[0:ny, 0:nx]
+    z = (10000.0 - 2.0 * x - y).astype(np.float32)
+    d8 = oracle.receivers_d8(z, 1.0, oracle.EDGE_ROUTE)
+    assert (d8[:-1, :-1] == 7).all()  # SE
+    d4 = oracle.receivers_d8(z, 1.0, oracle.EDGE_ROUTE | oracle.D4)
+    assert (d4[:, :-1] == 0).all()    # E
+    assert (d4[:-1, -1] == 3).all()   # S
+    assert d4[-1, -1] == oracle.SINK
+    order = oracle.high_to_low_order(z)
+    _, area = oracle.accumulate_d8(d4, order, None)
+    want = np.where(x < nx - 1, x + 1, nx * (y + 1)).astype(np.uint64)
+    np.testing.assert_array_equal(area, want)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_d4_dense_solve_and_codes(seed):
+    ny, nx = 17, 23
+    z = _dem(ny, nx, seed)
+    rain = inputs.rain_field(ny, nx, seed)
+    d = oracle.receivers_d8(z, 30.0, oracle.D4)
+    assert set(np.unique(d)) <= {0, 1, 2, 3, oracle.SINK}
+    # every D4 receiver is a strictly lower orthogonal neighbour
+    for yy in range(ny):
+        for xx in range(nx):
+            k = d[yy, xx]
+            if k != oracle.SINK:
+                assert z[yy + OFFY[k], xx + OFFX[k]] < z[yy, xx]
+    order = oracle.high_to_low_order(z)
+    w, _ = oracle.accumulate_d8(d, order, rain)
+    ref = np.linalg.solve(_dense_A_d8(d), rain.astype(np.float64).ravel())
+    np.testing.assert_allclose(w.ravel(), ref, rtol=1e-12)
