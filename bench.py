@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the MFD/batch/adjoint rows")
-    ap.add_argument("--rows", default="slope_split,batched,adjoint,d8_32768",
+    ap.add_argument("--rows", default="slope_split,batched,adjoint,d8_32768,richardson",
                     help="comma-separated extra rows to run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -393,6 +393,9 @@ def extra_rows(api, L, dev, peak, want):
     if "d8_32768" in want:
         rows["d8_32768"] = d8_large_row(api, L, dev, peak, timed)
         torch.cuda.empty_cache()
+    if "richardson" in want:
+        rows["richardson"] = richardson_row(api, dev, timed)
+        torch.cuda.empty_cache()
     return rows
 
 
@@ -454,6 +457,38 @@ def d8_large_row(api, L, dev, peak, timed):
             "accumulate_roofline": {"bound": "hbm", "algorithmic_bytes_per_cell": 9,
                                     "achieved_gbs": cells * 9 / (ms_acc * 1e-3) / 1e9, "peak": peak,
                                     "frac": cells * 9 / (ms_acc * 1e-3) / 1e9 / peak}}
+
+
+def richardson_row(api, dev, timed):
+    """The paper's Richardson I+X iteration on 64x32 tiles (one GPU) against
+    the two-launch exact solve, on the D8 step's DEM (4096^2, rain) and the
+    slope-split DEM (8192^2, unit rain): iterations and device time."""
+    import torch
+    from paper_2606_12800_gb300 import inputs
+    out = {}
+    n = N_SIDE
+    z = torch.from_numpy(inputs.fractal_dem(n, n, beta=2.0, tilt=0.01, seed=SEED, dx=DX)).to(dev)
+    rain = torch.from_numpy(inputs.rain_field(n, n, SEED)).to(dev)
+    R = api.routing_d8(api.receivers_d8(z, DX))
+    it = {}
+
+    def rich_d8():
+        it["n"] = api.accumulate_richardson(R, rain)[1]
+    ms_r = timed(rich_d8, reps=3)
+    ms_x = timed(lambda: api.accumulate(R, rain, want_w=True), reps=3)
+    out["d8_4096"] = {"iterations": it["n"], "richardson_ms": ms_r, "exact_two_phase_ms": ms_x}
+    del z, rain, R
+    n = MFD_SIDE
+    zt = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=SEED + 2, device="cuda")
+    m = api.receivers_mfd(zt, DX, 1.1)
+    Rm = api.routing_mfd(m, zt, DX, 1.1)
+
+    def rich_mfd():
+        it["n"] = api.accumulate_richardson(Rm, None)[1]
+    ms_r = timed(rich_mfd, reps=2)
+    ms_x = timed(lambda: api.accumulate(Rm, None, want_w=True, device=dev), reps=2)
+    out["mfd_8192"] = {"iterations": it["n"], "richardson_ms": ms_r, "exact_two_phase_ms": ms_x}
+    return out
 
 
 def batch_rows(api, L, dev):

@@ -174,6 +174,27 @@ fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_o
                         void* stream);
 
 /*
+ * The paper's own parallel solver, run on one GPU (Sec. 2.4, 3.3, App. B.1):
+ * Richardson iteration for the "I+X" form of A w = r,
+ *     w^(l+1) = D^{-1} (r + R w^(l)),     w^(0) = 0   (Eq. richardson-I+X),
+ * with 64x32 tiles as the subdomains: D^{-1} is each tile's exact high-to-low
+ * solve and R w passes water across tile boundaries.  A stream crossing tile
+ * boundaries C times is exact after C + 1 iterations; the loop stops at the
+ * first sweep that changes no value, so the result equals fr_accumulate's up
+ * to the order of additions (fixed here too).  Offered as the paper's method
+ * for comparison; fr_accumulate reaches the exact result in two launches.
+ *   w_out, w_lo_out as fr_accumulate (w_out required).
+ *   max_iterations  >= 1; FR_ERR_NO_PROGRESS if more would be needed.
+ *   iterations_out  host int32 or NULL: iterations until exact (C + 1).
+ * Synchronises the stream once per iteration.  Workspace as fr_accumulate.
+ */
+fr_status fr_accumulate_richardson(const fr_routing* routing, const float* rain, float* w_out,
+                                   float* w_lo_out, int32_t max_iterations,
+                                   int32_t* iterations_out, void* ws, size_t ws_bytes,
+                                   void* stream);
+
+/*
+ * Receivers + accumulation in one call (D8)/*
  * Receivers + accumulation in one call (D8): the direction grid goes to
  * dir_out if non-NULL, else to the workspace.  Outputs as fr_accumulate.
  * Workspace: fr_workspace_size(FR_OP_ROUTE, nx, ny, flags).

@@ -49,7 +49,7 @@ FR_NOALLOC_MAX_CELLS = 1 << 20
 EXPORTS = (
     "fr_receivers_d8", "fr_receivers_mfd", "fr_accumulate", "fr_route_d8", "fr_route_mfd",
     "fr_route_adjoint", "fr_mass_balance", "fr_route_batch", "fr_batch_workspace_size",
-    "fr_batch_autotune", "fr_route_d8_noalloc",
+    "fr_batch_autotune", "fr_route_d8_noalloc", "fr_accumulate_richardson",
     "fr_workspace_size", "fr_get_status", "fr_status_string", "fr_version",
 )
 
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
             "fr_receivers_d8": (S, [P, I64, I64, D, U32, P, P, P]),
             "fr_receivers_mfd": (S, [P, I64, I64, D, D, U32, P, P, P, P]),
             "fr_accumulate": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, ctypes.c_size_t, P]),
+            "fr_accumulate_richardson": (S, [ctypes.POINTER(fr_routing), P, P, P, I32,
+                                             ctypes.POINTER(ctypes.c_int32), P, ctypes.c_size_t, P]),
             "fr_route_d8": (S, [P, I64, I64, D, U32, P, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_mfd": (S, [P, I64, I64, D, D, U32, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_d8_noalloc": (S, [P, I64, I64, D, U32, P, P, P, P, P, P]),

@@ -186,6 +186,28 @@ def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
     return out
 
 
+def accumulate_richardson(R: fr_routing, rain: Optional[torch.Tensor] = None,
+                          max_iterations: int = 10000, want_lo: bool = False, device=None):
+    """The paper's Richardson I+X iteration on 64x32 tiles
+    (fr_accumulate_richardson): ({"w", "w_lo"}, iterations until exact)."""
+    ny, nx = R.ny, R.nx
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    if rain is not None:
+        _check_grid(rain, torch.float32, "rain")
+        dev = rain.device
+    w = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
+    ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
+    it = ctypes.c_int32(0)
+    check(load().fr_accumulate_richardson(ctypes.byref(R), _p(rain), _p(w), _p(lo),
+                                          int(max_iterations), ctypes.byref(it), _p(ws),
+                                          ws.numel(), _stream()), "fr_accumulate_richardson")
+    out = {"w": w}
+    if lo is not None:
+        out["w_lo"] = lo
+    return out, int(it.value)
+
+
 def adjoint(R: fr_routing, w: torch.Tensor, w_lo: Optional[torch.Tensor] = None,
             dLdw: Optional[torch.Tensor] = None, want_dz: bool = False):
     """(dL/dr, dL/dz or None) for L = sum over sinks of w^2, or for the

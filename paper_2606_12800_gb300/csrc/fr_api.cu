@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <utility>
 
 #include "../../include/fr.h"
 #include "fr_internal.h"
@@ -238,6 +239,48 @@ fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, fl
                         uint64_t* area_out, void* ws, size_t ws_bytes, void* stream) {
     return accumulate_impl(R, rain, w_out, w_lo_out, area_out, ws, ws_bytes, (cudaStream_t)stream,
                            false);
+}
+
+fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float* w_out,
+                                   float* w_lo_out, int32_t max_iterations,
+                                   int32_t* iterations_out, void* ws, size_t ws_bytes,
+                                   void* stream) {
+    if (!routing_ok(R) || !w_out || max_iterations < 1) return FR_ERR_INVALID_ARG;
+    const bool mfd = R->kind == FR_ROUTING_MFD;
+    const int64_t n = R->nx * R->ny;
+    if (!(mfd ? ws_ok_mfd(ws, ws_bytes, n) : ws_ok(ws, ws_bytes, n))) return FR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prob P = base_prob(R, (char*)ws);
+    P.init = rain;
+    const Layout L = layout(n);
+    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p,
+                                    reinterpret_cast<float*>((char*)ws + L.frac), s) != cudaSuccess)
+        return FR_ERR_CUDA;
+    // two iterates (interleaved two-float) in the frontier and list regions
+    float2* a = reinterpret_cast<float2*>((char*)ws + L.glist);
+    float2* b = reinterpret_cast<float2*>((char*)ws + L.link);
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);  // globals block
+    if (cudaMemsetAsync(a, 0, (size_t)n * sizeof(float2), s) != cudaSuccess) return FR_ERR_CUDA;
+    int32_t it = 0;
+    bool converged = false;
+    for (int32_t sweep = 1; sweep <= max_iterations + 1; ++sweep) {
+        unsigned long long h[2] = {0, 0};
+        if (cudaMemsetAsync(counts, 0, sizeof(h), s) != cudaSuccess) return FR_ERR_CUDA;
+        if (richardson_sweep(mfd, P, a, b, counts, s) != cudaSuccess) return FR_ERR_CUDA;
+        if (cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return FR_ERR_CUDA;
+        if (h[1] != (unsigned long long)n) return FR_ERR_NO_PROGRESS;  // a cycle
+        std::swap(a, b);  // a: the newest iterate
+        if (h[0] == 0) {
+            converged = true;
+            break;
+        }
+        it = sweep;
+    }
+    if (iterations_out) *iterations_out = it;
+    if (!converged) return FR_ERR_NO_PROGRESS;
+    return cuda_status(richardson_output(a, n, w_out, w_lo_out, s));
 }
 
 fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,

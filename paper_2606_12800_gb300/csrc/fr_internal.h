@@ -87,6 +87,12 @@ cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t*
                                 const float* rain, const float* w, const float* w_lo,
                                 const uint64_t* area, double* partials, int nblocks,
                                 double* out, cudaStream_t s);
+// Richardson I+X (fr_richardson.cu): one sweep prev -> next over 64x32
+// subdomains (counts[0] += changed cells, counts[1] += finalised cells), and
+// the copy of converged two-float values into the outputs.
+cudaError_t richardson_sweep(bool mfd, const Prob& P, const float2* prev, float2* next,
+                             unsigned long long* counts, cudaStream_t s);
+cudaError_t richardson_output(const float2* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 cudaError_t launch_mfd_fractions(const float* z, const uint8_t* mask, int64_t nx, int64_t ny,
                                  double dx, double p, float* frac, cudaStream_t s);
 cudaError_t launch_receivers_batch(int kind, const Prob* probs, const int64_t* prefix, int nprob,

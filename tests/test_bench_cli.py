@@ -11,8 +11,8 @@ sys.path.insert(0, str(ROOT))
 
 def test_default_rows_have_functions():
     import bench
-    for name in ("extra_rows", "batch_rows", "adjoint_row", "d8_large_row", "cpu_baseline",
-                 "run_reference"):
+    for name in ("extra_rows", "batch_rows", "adjoint_row", "d8_large_row", "richardson_row",
+                 "cpu_baseline", "run_reference"):
         assert callable(getattr(bench, name)), name
 
 

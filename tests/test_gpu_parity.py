@@ -337,6 +337,74 @@ def test_mfd_adjoint_finite_differences_full_size(api):
     _adjoint_fd_check(api, zt, 64, seed=64)
 
 
+def _crossings(order, deps, nx, tx=64, ty=32):
+    """C = the largest number of 64x32-tile boundaries a dependency path
+    crosses (cells in high-to-low order; deps[c] = cells c receives from)."""
+    cross = np.zeros(len(order), np.int64)
+    tile = lambda c: ((c % nx) // tx, (c // nx) // ty)
+    for c in order:
+        for j in deps.get(int(c), ()):
+            cross[c] = max(cross[c], cross[j] + (tile(j) != tile(int(c))))
+    return int(cross.max()) if len(cross) else 0
+
+
+def _donor_lists(recv_of, n):
+    deps = {}
+    for j in range(n):
+        for t in recv_of(j):
+            deps.setdefault(t, []).append(j)
+    return deps
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (97, 131), (256, 300)])
+def test_richardson_d8_exact_after_c_plus_one(api, shape):
+    """Richardson I+X on 64x32 tiles: the result of the exact solve, after
+    exactly C + 1 iterations (C = most tile crossings of any stream)."""
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.0, tilt=0.01, seed=nx)
+    d = api.receivers_d8(cuda(z), 30.0)
+    R = api.routing_d8(d)
+    out, iters = api.accumulate_richardson(R, None)
+    d_ref, w_ref, _, order = oracle.route_d8(z, 30.0, None)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    dr = d_ref.ravel()
+    recv = lambda j: () if dr[j] == oracle.SINK else (j + oracle.OFFY[dr[j]] * nx + oracle.OFFX[dr[j]],)
+    assert iters == _crossings(order, _donor_lists(recv, nx * ny), nx) + 1
+    rain = inputs.rain_field(ny, nx, 2)
+    out, _ = api.accumulate_richardson(R, cuda(rain))
+    _, w_ref, _, _ = oracle.route_d8(z, 30.0, rain)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+@pytest.mark.parametrize("shape", [(70, 90), (200, 257)])
+def test_richardson_mfd_exact_after_c_plus_one(api, shape):
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=ny)
+    zt = cuda(z)
+    m = api.receivers_mfd(zt, 30.0, 1.1)
+    R = api.routing_mfd(m, zt, 30.0, 1.1)
+    out, iters = api.accumulate_richardson(R, None)
+    m_ref, _, w_ref, order = oracle.route_mfd(z, 30.0, 1.1, None)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    mr = m_ref.ravel()
+    recv = lambda j: tuple(j + oracle.OFFY[k] * nx + oracle.OFFX[k] for k in range(8) if (mr[j] >> k) & 1)
+    assert iters == _crossings(order, _donor_lists(recv, nx * ny), nx) + 1
+    # the same water as the two-phase exact solve
+    w2 = api.accumulate(R, None, want_w=True)["w"]
+    assert relerr(out["w"].cpu().numpy(), w2.cpu().numpy().astype(np.float64)) <= 1e-6
+
+
+def test_richardson_stops_at_the_iteration_limit(api):
+    z = inputs.planar_dem(40, 300, 0.01, 30.0)  # rows are chains across 5 tiles
+    d = api.receivers_d8(cuda(z), 30.0, oracle.EDGE_ROUTE)
+    R = api.routing_d8(d)
+    with pytest.raises(Exception):
+        api.accumulate_richardson(R, None, max_iterations=2)
+    out, iters = api.accumulate_richardson(R, None, max_iterations=50)
+    assert iters == 5  # C = 4 crossings along a 300-cell row
+    np.testing.assert_allclose(out["w"].cpu().numpy()[5, :], np.arange(1, 301), rtol=0)
+
+
 def _batch_specs():
     return [(17, 23, 2.0), (64, 64, 1.8), (31, 200, 2.4), (130, 97, 2.1), (300, 257, 2.0),
             (5, 5, 2.2), (1, 40, 2.0), (90, 1, 2.0), (256, 300, 1.9), (128, 64, 2.3)]
