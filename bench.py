@@ -472,22 +472,28 @@ def richardson_row(api, dev, timed):
     R = api.routing_d8(api.receivers_d8(z, DX))
     it = {}
 
-    def rich_d8():
-        it["n"] = api.accumulate_richardson(R, rain)[1]
-    ms_r = timed(rich_d8, reps=3)
+    def rich_d8(order):
+        it[order] = api.accumulate_richardson(R, rain, order=order)[1]
+    ms_r1 = timed(lambda: rich_d8(1), reps=3)
+    ms_r2 = timed(lambda: rich_d8(2), reps=3)
     ms_x = timed(lambda: api.accumulate(R, rain, want_w=True), reps=3)
-    out["d8_4096"] = {"iterations": it["n"], "richardson_ms": ms_r, "exact_two_phase_ms": ms_x}
+    out["d8_4096"] = {"i_plus_x": {"iterations": it[1], "ms": ms_r1},
+                      "i_minus_x_i_plus_x": {"iterations": it[2], "ms": ms_r2},
+                      "exact_two_phase_ms": ms_x}
     del z, rain, R
     n = MFD_SIDE
     zt = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=SEED + 2, device="cuda")
     m = api.receivers_mfd(zt, DX, 1.1)
     Rm = api.routing_mfd(m, zt, DX, 1.1)
 
-    def rich_mfd():
-        it["n"] = api.accumulate_richardson(Rm, None)[1]
-    ms_r = timed(rich_mfd, reps=2)
+    def rich_mfd(order):
+        it[order] = api.accumulate_richardson(Rm, None, order=order)[1]
+    ms_r1 = timed(lambda: rich_mfd(1), reps=2)
+    ms_r2 = timed(lambda: rich_mfd(2), reps=2)
     ms_x = timed(lambda: api.accumulate(Rm, None, want_w=True, device=dev), reps=2)
-    out["mfd_8192"] = {"iterations": it["n"], "richardson_ms": ms_r, "exact_two_phase_ms": ms_x}
+    out["mfd_8192"] = {"i_plus_x": {"iterations": it[1], "ms": ms_r1},
+                       "i_minus_x_i_plus_x": {"iterations": it[2], "ms": ms_r2},
+                       "exact_two_phase_ms": ms_x}
     return out
 
 

@@ -174,22 +174,28 @@ fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_o
                         void* stream);
 
 /*
- * The paper's own parallel solver, run on one GPU (Sec. 2.4, 3.3, App. B.1):
- * Richardson iteration for the "I+X" form of A w = r,
- *     w^(l+1) = D^{-1} (r + R w^(l)),     w^(0) = 0   (Eq. richardson-I+X),
- * with 64x32 tiles as the subdomains: D^{-1} is each tile's exact high-to-low
- * solve and R w passes water across tile boundaries.  A stream crossing tile
- * boundaries C times is exact after C + 1 iterations; the loop stops at the
- * first sweep that changes no value, so the result equals fr_accumulate's up
- * to the order of additions (fixed here too).  Offered as the paper's method
- * for comparison; fr_accumulate reaches the exact result in two launches.
- *   w_out, w_lo_out as fr_accumulate (w_out required).
- *   max_iterations  >= 1; FR_ERR_NO_PROGRESS if more would be needed.
- *   iterations_out  host int32 or NULL: iterations until exact (C + 1).
- * Synchronises the stream once per iteration.  Workspace as fr_accumulate.
+ * The paper's own parallel solver, run on one GPU (Sec. 2.4, 3.3, 3.4,
+ * App. B.1): Richardson iteration for the "I+X" form of A w = r,
+ *     w^(l+1) = T(w^(l)),  T(w) = D^{-1} (r + R w),  w^(0) = 0
+ * (Eq. richardson-I+X), with 64x32 tiles as the subdomains: D^{-1} is each
+ * tile's exact high-to-low solve and R w passes water across tile
+ * boundaries.  order = 1 is I+X.  order = 2 is the (I-X)(I+X) scheme of
+ * Sec. 3.4: one Richardson step on the preconditioned system equals two
+ * applications of T; order = k applies T k times per iteration (the longer
+ * preconditioner series Sec. 3.4 mentions).  A stream crossing tile
+ * boundaries C times is exact after C + 1 applications of T, that is after
+ * ceil((C + 1) / order) iterations.  The loop stops at the first sweep that
+ * changes no value; the result equals fr_accumulate's up to the order of
+ * additions (also fixed here).  Offered as the paper's method for
+ * comparison: fr_accumulate reaches the exact result in two launches.
+ *   w_out, w_lo_out  as fr_accumulate (w_out required).
+ *   order            1 .. 64.
+ *   max_iterations   >= 1; FR_ERR_NO_PROGRESS if more would be needed.
+ *   iterations_out   host int32 or NULL: iterations until exact.
+ * Synchronises the stream after every sweep.  Workspace as fr_accumulate.
  */
 fr_status fr_accumulate_richardson(const fr_routing* routing, const float* rain, float* w_out,
-                                   float* w_lo_out, int32_t max_iterations,
+                                   float* w_lo_out, int32_t order, int32_t max_iterations,
                                    int32_t* iterations_out, void* ws, size_t ws_bytes,
                                    void* stream);
 

@@ -102,7 +102,7 @@ def load(build_if_missing: bool = True):
             "fr_receivers_d8": (S, [P, I64, I64, D, U32, P, P, P]),
             "fr_receivers_mfd": (S, [P, I64, I64, D, D, U32, P, P, P, P]),
             "fr_accumulate": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, ctypes.c_size_t, P]),
-            "fr_accumulate_richardson": (S, [ctypes.POINTER(fr_routing), P, P, P, I32,
+            "fr_accumulate_richardson": (S, [ctypes.POINTER(fr_routing), P, P, P, I32, I32,
                                              ctypes.POINTER(ctypes.c_int32), P, ctypes.c_size_t, P]),
             "fr_route_d8": (S, [P, I64, I64, D, U32, P, P, P, P, P, P, ctypes.c_size_t, P]),
             "fr_route_mfd": (S, [P, I64, I64, D, D, U32, P, P, P, P, P, ctypes.c_size_t, P]),

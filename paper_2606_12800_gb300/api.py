@@ -186,10 +186,10 @@ def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
     return out
 
 
-def accumulate_richardson(R: fr_routing, rain: Optional[torch.Tensor] = None,
+def accumulate_richardson(R: fr_routing, rain: Optional[torch.Tensor] = None, order: int = 1,
                           max_iterations: int = 10000, want_lo: bool = False, device=None):
-    """The paper's Richardson I+X iteration on 64x32 tiles
-    (fr_accumulate_richardson): ({"w", "w_lo"}, iterations until exact)."""
+    """The paper's Richardson iteration on 64x32 tiles (fr_accumulate_richardson;
+    order 1: I+X, order 2: (I-X)(I+X)): ({"w", "w_lo"}, iterations until exact)."""
     ny, nx = R.ny, R.nx
     dev = device or torch.device("cuda", torch.cuda.current_device())
     if rain is not None:
@@ -199,7 +199,7 @@ def accumulate_richardson(R: fr_routing, rain: Optional[torch.Tensor] = None,
     lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
     ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
     it = ctypes.c_int32(0)
-    check(load().fr_accumulate_richardson(ctypes.byref(R), _p(rain), _p(w), _p(lo),
+    check(load().fr_accumulate_richardson(ctypes.byref(R), _p(rain), _p(w), _p(lo), int(order),
                                           int(max_iterations), ctypes.byref(it), _p(ws),
                                           ws.numel(), _stream()), "fr_accumulate_richardson")
     out = {"w": w}

@@ -242,10 +242,11 @@ fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, fl
 }
 
 fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float* w_out,
-                                   float* w_lo_out, int32_t max_iterations,
+                                   float* w_lo_out, int32_t order, int32_t max_iterations,
                                    int32_t* iterations_out, void* ws, size_t ws_bytes,
                                    void* stream) {
-    if (!routing_ok(R) || !w_out || max_iterations < 1) return FR_ERR_INVALID_ARG;
+    if (!routing_ok(R) || !w_out || max_iterations < 1 || order < 1 || order > 64)
+        return FR_ERR_INVALID_ARG;
     const bool mfd = R->kind == FR_ROUTING_MFD;
     const int64_t n = R->nx * R->ny;
     if (!(mfd ? ws_ok_mfd(ws, ws_bytes, n) : ws_ok(ws, ws_bytes, n))) return FR_ERR_WORKSPACE;
@@ -261,9 +262,12 @@ fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float
     float2* b = reinterpret_cast<float2*>((char*)ws + L.link);
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);  // globals block
     if (cudaMemsetAsync(a, 0, (size_t)n * sizeof(float2), s) != cudaSuccess) return FR_ERR_CUDA;
-    int32_t it = 0;
+    // one iteration = `order` sweeps; the sweep after the last changing one
+    // shows that the iterate is exact
+    int32_t exact_after = 0;  // sweeps
     bool converged = false;
-    for (int32_t sweep = 1; sweep <= max_iterations + 1; ++sweep) {
+    const int64_t max_sweeps = (int64_t)max_iterations * order + 1;
+    for (int64_t sweep = 1; sweep <= max_sweeps; ++sweep) {
         unsigned long long h[2] = {0, 0};
         if (cudaMemsetAsync(counts, 0, sizeof(h), s) != cudaSuccess) return FR_ERR_CUDA;
         if (richardson_sweep(mfd, P, a, b, counts, s) != cudaSuccess) return FR_ERR_CUDA;
@@ -276,10 +280,11 @@ fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float
             converged = true;
             break;
         }
-        it = sweep;
+        exact_after = (int32_t)sweep;
     }
-    if (iterations_out) *iterations_out = it;
-    if (!converged) return FR_ERR_NO_PROGRESS;
+    const int32_t iterations = (exact_after + order - 1) / order;
+    if (iterations_out) *iterations_out = iterations;
+    if (!converged || iterations > max_iterations) return FR_ERR_NO_PROGRESS;
     return cuda_status(richardson_output(a, n, w_out, w_lo_out, s));
 }
 

@@ -369,7 +369,12 @@ def test_richardson_d8_exact_after_c_plus_one(api, shape):
     assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
     dr = d_ref.ravel()
     recv = lambda j: () if dr[j] == oracle.SINK else (j + oracle.OFFY[dr[j]] * nx + oracle.OFFX[dr[j]],)
-    assert iters == _crossings(order, _donor_lists(recv, nx * ny), nx) + 1
+    C = _crossings(order, _donor_lists(recv, nx * ny), nx)
+    assert iters == C + 1
+    # (I-X)(I+X): two applications per iteration, half the iterations
+    out2, iters2 = api.accumulate_richardson(R, None, order=2)
+    assert iters2 == (C + 2) // 2
+    np.testing.assert_array_equal(out2["w"].cpu().numpy(), out["w"].cpu().numpy())
     rain = inputs.rain_field(ny, nx, 2)
     out, _ = api.accumulate_richardson(R, cuda(rain))
     _, w_ref, _, _ = oracle.route_d8(z, 30.0, rain)
@@ -402,6 +407,8 @@ def test_richardson_stops_at_the_iteration_limit(api):
         api.accumulate_richardson(R, None, max_iterations=2)
     out, iters = api.accumulate_richardson(R, None, max_iterations=50)
     assert iters == 5  # C = 4 crossings along a 300-cell row
+    assert api.accumulate_richardson(R, None, order=2)[1] == 3
+    assert api.accumulate_richardson(R, None, order=5)[1] == 1
     np.testing.assert_allclose(out["w"].cpu().numpy()[5, :], np.arange(1, 301), rtol=0)
 
 
