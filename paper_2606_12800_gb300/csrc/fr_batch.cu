@@ -173,7 +173,7 @@ bool tiles_ok(const fr_tile* t, int n, int kind) {
 // receiver stage, and the halo-tile geometry of the D8 local stage
 // (0: 128x32 inner tiles, 1: 64x32).
 struct Tune {
-    int recv = 8, geo = 0;
+    int recv = 8, geo = 1;
 };
 Tune g_tune[2];
 std::mutex g_tune_mutex;

@@ -507,8 +507,8 @@ cudaError_t launch_d8_batch(const Prob* probs, const int64_t* prefix, int nprob,
     return launch_global<Mode::FwdD8, W, AREA>(probs, none, G, total_cells, s);
 }
 
-using GeoD8 = D8Geo<kD8TileX, kD8TileY>;        // geometry 0
-using GeoD8s = D8Geo<kD8TileX / 2, kD8TileY>;   // geometry 1: narrower tiles, 3 CTAs per SM
+using GeoD8 = D8Geo<kD8TileX, kD8TileY>;        // geometry 0: 128x32
+using GeoD8s = D8Geo<kD8TileX / 2, kD8TileY>;   // geometry 1: 64x32, three CTAs per SM
 
 template <class Gm>
 cudaError_t d8_batch_w(bool want_w, bool want_area, const Prob* probs, const int64_t* prefix,
@@ -524,9 +524,10 @@ cudaError_t d8_batch_w(bool want_w, bool want_area, const Prob* probs, const int
 // D8 forward accumulation: halo-tile local phase + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& P, EngineGlobals* G,
                               cudaStream_t s) {
-    if (want_w && want_area) return launch_d8<GeoD8, true, true>(P, G, s);
-    if (want_w) return launch_d8<GeoD8, true, false>(P, G, s);
-    return launch_d8<GeoD8, false, true>(P, G, s);
+    // 64x32 inner tiles: measured fastest at 4096^2 (three CTAs per SM)
+    if (want_w && want_area) return launch_d8<GeoD8s, true, true>(P, G, s);
+    if (want_w) return launch_d8<GeoD8s, true, false>(P, G, s);
+    return launch_d8<GeoD8s, false, true>(P, G, s);
 }
 
 // Batched D8 forward: the CTAs of all problems' tiles in one launch (tile
