@@ -62,7 +62,8 @@ struct SmemD8 {
     alignas(16) uint8_t code[Gm::RY * Gm::CP];  // receiver codes of region + ring, padded rows
     alignas(16) uint8_t nbp[Gm::RY * Gm::CP];   // 1 where a region cell is not bare
     uint16_t queue[NE];            // level lists, appended one after another
-    int qtail;
+    int qtail;                     // end of the start list (the first level)
+    int lcnt[3];                   // sizes of the levels being appended (rotating)
     unsigned long long done;
 };
 
@@ -184,7 +185,10 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
                      (!W || ((uintptr_t)P.out_hi & 15) == 0) &&
                      (!AREA || ((uintptr_t)P.area & 15) == 0);
     uint8_t* stb = reinterpret_cast<uint8_t*>(S.st);
-    if (tid == 0) S.qtail = 0;
+    if (tid == 0) {
+        S.qtail = 0;
+        S.lcnt[0] = S.lcnt[1] = S.lcnt[2] = 0;
+    }
 
     if (vec) {
         // ---- asynchronous copies: code rows (8-byte chunks; byte b <-> grid
@@ -359,8 +363,14 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
     // ---- levels: finalise each level's list, collect the next one
     {
         const unsigned lane = tid & 31u;
-        int lo = 0, hi = S.qtail;
+        // level L appends the next level after its own end `hi`, counting in
+        // lcnt[(L + 1) % 3]; thread 0 clears lcnt[(L + 2) % 3], last read before
+        // the previous barrier and next used after this level's barrier, so one
+        // barrier per level orders everything
+        int lo = 0, hi = S.qtail, level = 0;
         while (lo < hi) {
+            if (tid == 0) S.lcnt[(level + 2) % 3] = 0;
+            int* const lcnt = &S.lcnt[(level + 1) % 3];
             for (int base = lo; base < hi; base += NT8) {
                 const int i = base + tid;
                 int push = -1;
@@ -399,15 +409,15 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
                 const unsigned pm = __ballot_sync(0xffffffffu, push >= 0);
                 if (pm) {
                     int b0 = 0;
-                    if (lane == (unsigned)(__ffs(pm) - 1)) b0 = atomicAdd(&S.qtail, __popc(pm));
+                    if (lane == (unsigned)(__ffs(pm) - 1)) b0 = hi + atomicAdd(lcnt, __popc(pm));
                     b0 = __shfl_sync(0xffffffffu, b0, __ffs(pm) - 1);
                     if (push >= 0) S.queue[b0 + __popc(pm & ((1u << lane) - 1u))] = (uint16_t)push;
                 }
             }
             __syncthreads();  // the level's values and the next list are complete
             lo = hi;
-            hi = S.qtail;
-            __syncthreads();  // everybody has read the new end before the next appends
+            hi += *lcnt;
+            ++level;
         }
     }
 

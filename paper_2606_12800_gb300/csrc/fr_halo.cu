@@ -70,6 +70,7 @@ struct SmemHalo {
     uint8_t tm[NE];       // in-region targets (receivers forward, donors adjoint)
     uint8_t fin[NE];      // 1 final, 0 pending, 0x0F outside the grid
     int qtail;
+    int lcnt[3];          // sizes of the levels being appended (rotating)
     unsigned long long done;
 };
 
@@ -87,12 +88,15 @@ __device__ __forceinline__ void mark_global_cell(const Prob& P, EngineGlobals* G
 }
 
 // Warp-aggregated append of one optional cell per lane (all lanes call).
-__device__ __forceinline__ void push_cell(SmemHalo& S, int cell) {
+// (with cnt: appends after position `end`, counting in *cnt; the start list
+// uses the queue tail itself)
+__device__ __forceinline__ void push_cell(SmemHalo& S, int cell, int end = 0, int* cnt = nullptr) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned pm = __ballot_sync(0xffffffffu, cell >= 0);
     if (!pm) return;
     int b0 = 0;
-    if (lane == (unsigned)(__ffs(pm) - 1)) b0 = atomicAdd(&S.qtail, __popc(pm));
+    if (lane == (unsigned)(__ffs(pm) - 1))
+        b0 = cnt ? end + atomicAdd(cnt, __popc(pm)) : atomicAdd(&S.qtail, __popc(pm));
     b0 = __shfl_sync(0xffffffffu, b0, __ffs(pm) - 1);
     if (cell >= 0) S.queue[b0 + __popc(pm & ((1u << lane) - 1u))] = (uint16_t)cell;
 }
@@ -133,7 +137,10 @@ __global__ void __launch_bounds__(kHaloNT, 3) k_local_halo(Prob Pone, EngineGlob
     const int64_t ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int64_t x0 = tx * TX, y0 = ty * TY;
     const int64_t ox = x0 - H - 1, oy = y0 - H - 1;  // ring origin (may be negative)
-    if (tid == 0) S.qtail = 0;
+    if (tid == 0) {
+        S.qtail = 0;
+        S.lcnt[0] = S.lcnt[1] = S.lcnt[2] = 0;
+    }
 
     // ---- region + ring: receiver masks
     for (int i = tid; i < NR; i += NT) {
@@ -225,8 +232,13 @@ __global__ void __launch_bounds__(kHaloNT, 3) k_local_halo(Prob Pone, EngineGlob
 
     // ---- levels: finalise each level's list, collect the next one
     {
-        int lo = 0, hi = S.qtail;
+        // level L appends after its own end `hi`, counting in lcnt[(L + 1) % 3];
+        // thread 0 clears lcnt[(L + 2) % 3] (last read before the previous
+        // barrier, next used after this one): one barrier per level
+        int lo = 0, hi = S.qtail, level = 0;
         while (lo < hi) {
+            if (tid == 0) S.lcnt[(level + 2) % 3] = 0;
+            int* const lcnt = &S.lcnt[(level + 1) % 3];
             for (int base = lo; base < hi; base += NT) {
                 const int i = base + tid;
                 int c = 0;
@@ -282,13 +294,13 @@ __global__ void __launch_bounds__(kHaloNT, 3) k_local_halo(Prob Pone, EngineGlob
                         ready &= ready - 1;
                         cell = c + offy(k) * EX + offx(k);
                     }
-                    push_cell(S, cell);
+                    push_cell(S, cell, hi, lcnt);
                 }
             }
             __syncthreads();  // the level's values and the next list are complete
             lo = hi;
-            hi = S.qtail;
-            __syncthreads();  // everybody has read the new end before the next appends
+            hi += *lcnt;
+            ++level;
         }
     }
 

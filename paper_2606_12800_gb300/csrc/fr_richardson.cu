@@ -32,15 +32,17 @@ struct SmemRich {
     uint8_t tm[kRNC];         // in-tile receivers
     uint8_t fin[kRNC];        // 1 final, 0 pending, 0x0F outside the grid
     int qtail;
+    int lcnt[3];              // sizes of the levels being appended (rotating)
     unsigned long long changed, done;
 };
 
-__device__ __forceinline__ void push_rich(SmemRich& S, int cell) {
+__device__ __forceinline__ void push_rich(SmemRich& S, int cell, int end = 0, int* cnt = nullptr) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned pm = __ballot_sync(0xffffffffu, cell >= 0);
     if (!pm) return;
     int b0 = 0;
-    if (lane == (unsigned)(__ffs(pm) - 1)) b0 = atomicAdd(&S.qtail, __popc(pm));
+    if (lane == (unsigned)(__ffs(pm) - 1))
+        b0 = cnt ? end + atomicAdd(cnt, __popc(pm)) : atomicAdd(&S.qtail, __popc(pm));
     b0 = __shfl_sync(0xffffffffu, b0, __ffs(pm) - 1);
     if (cell >= 0) S.queue[b0 + __popc(pm & ((1u << lane) - 1u))] = (uint16_t)cell;
 }
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(kRNT) k_richardson_sweep(Prob P, const float2*
     const int64_t x0 = tx * TX, y0 = ty * TY;
     if (tid == 0) {
         S.qtail = 0;
+        S.lcnt[0] = S.lcnt[1] = S.lcnt[2] = 0;
         S.changed = 0;
         S.done = 0;
     }
@@ -106,9 +109,11 @@ __global__ void __launch_bounds__(kRNT) k_richardson_sweep(Prob P, const float2*
         push_rich(S, (c < NC && S.fin[c] == 0 && S.dm[c] == 0) ? c : -1);
     }
     __syncthreads();
-    int lo = 0, hi = S.qtail;
+    int lo = 0, hi = S.qtail, level = 0;
     unsigned long long nchanged = 0, ndone = 0;
     while (lo < hi) {
+        if (tid == 0) S.lcnt[(level + 2) % 3] = 0;  // one barrier per level (as fr_halo.cu)
+        int* const lcnt = &S.lcnt[(level + 1) % 3];
         for (int base = lo; base < hi; base += NT) {
             const int i = base + tid;
             int c = 0;
@@ -160,13 +165,13 @@ __global__ void __launch_bounds__(kRNT) k_richardson_sweep(Prob P, const float2*
                     ready &= ready - 1;
                     cell = c + offy(k) * TX + offx(k);
                 }
-                push_rich(S, cell);
+                push_rich(S, cell, hi, lcnt);
             }
         }
         __syncthreads();
         lo = hi;
-        hi = S.qtail;
-        __syncthreads();
+        hi += *lcnt;
+        ++level;
     }
     for (int o = 16; o; o >>= 1) {
         nchanged += __shfl_down_sync(0xffffffffu, nchanged, o);
