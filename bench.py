@@ -111,14 +111,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def dist_init(n):
+def dist_init(n, backend="nccl"):
+    """One process per GPU (torchrun sets RANK / LOCAL_RANK / WORLD_SIZE /
+    MASTER_*); the replicas share nothing but the barrier and the timing."""
     import torch
     if n <= 1:
         return 0, 1
     import torch.distributed as dist
-    dist.init_process_group("nccl")
+    dist.init_process_group(backend)
     rank = dist.get_rank()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+    if backend == "nccl":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
     return rank, dist.get_world_size()
 
 
@@ -129,13 +132,21 @@ def barrier(world):
 
 
 def allmax(x, world):
+    """The largest x over all ranks (the slowest replica sets the job time)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world, steps, cells, total_ms):
+    """Whole-job throughput: the cells of every rank's steps over the slowest
+    rank's time (weak scaling: each replica routes its own DEM)."""
+    return world * steps * cells / (total_ms * 1e-3)
 
 
 # ----------------------------------------------------------------- reference
@@ -261,7 +272,7 @@ def main():
             clk = clk2
 
     cells = n * n
-    value = world * K * cells / (total_ms * 1e-3)
+    value = job_value(world, K, cells, total_ms)
     peak, peak_kind = peaks()
     acc_bytes = cells * (1 + 4 + 4 + 8)     # dir + rain in, w + area out
     acc_avg = statistics.mean(acc_ms) * 1e-3
