@@ -29,6 +29,8 @@
 // D8 areas are exact integers.
 #pragma once
 
+#include <cuda/atomic>
+
 #include "fr_internal.h"
 
 namespace fr {
@@ -88,6 +90,16 @@ __device__ __forceinline__ void wr_area(const Prob& P, int64_t i, uint64_t v) {
 }
 __device__ __forceinline__ uint32_t cnt_add(const Prob& P, int64_t i, uint32_t n) {
     return FR_OK(i, ncell(P), 5) ? counter_add(P.cnt, i, n) : 0xFFu;
+}
+// The same with acquire-release order at device scope: the caller's earlier
+// writes are visible to whoever completes the counter, and the completer sees
+// every earlier adder's writes.
+__device__ __forceinline__ uint32_t cnt_add_acq_rel(const Prob& P, int64_t i, uint32_t n) {
+    if (!FR_OK(i, ncell(P), 5)) return 0xFFu;
+    const uint32_t sh = 8u * (uint32_t)(i & 3);
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(P.cnt[i >> 2]);
+    const uint32_t old = w.fetch_add(n << sh, cuda::memory_order_acq_rel);
+    return ((old >> sh) & 0xFFu) + n;
 }
 
 template <class E>
@@ -211,6 +223,7 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
 }
 
 constexpr unsigned kStatusNoProgress = 5u;
+constexpr uint32_t kReadyAt = 16u;  // preset counters: > 8 dependencies, < 256 (one byte)
 
 __device__ __forceinline__ bool gbit(const Prob& P, int64_t i) {
     return FR_OK(i, ncell(P), 15) ? ((__ldg(P.gbits + (i >> 5)) >> (i & 31)) & 1u) : false;
@@ -238,13 +251,14 @@ __device__ __noinline__ unsigned long long walker_d8(const Prob& P, int64_t star
     while (true) {
         // window of routing bytes: code of neighbour k (0xFF outside the grid)
         uint8_t nb[8];
-        uint32_t gm = 0;
+        uint32_t gm = 0, gn = 0;  // in-grid neighbours; global neighbours
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int64_t xn = x + offx(k), yn = y + offy(k);
             const bool in = xn >= 0 && yn >= 0 && xn < P.nx && yn < P.ny;
             gm |= (uint32_t)in << k;
             nb[k] = in ? rd_rb(P, cur + offi(k, P.nx)) : (uint8_t)0xFF;
+            gn |= (uint32_t)(in && gbit(P, cur + offi(k, P.nx))) << k;
         }
         const uint8_t own = rd_rb(P, cur);
         uint32_t dm = 0;
@@ -274,50 +288,63 @@ __device__ __noinline__ unsigned long long walker_d8(const Prob& P, int64_t star
             wr_area(P, cur, s);
         }
         ++n;
-        __threadfence();
         if (own >= 8 || !((gm >> own) & 1u)) break;
+        if (!((gn >> own) & 1u)) break;  // the receiver was solved exactly by its own tile
+        // the receiver's counter was preset to kReadyAt - (its global donors):
+        // the adder that completes it continues there
         const int64_t u = cur + offi(own, P.nx);
-        if (!gbit(P, u)) break;  // solved exactly by its own tile
-        const uint32_t got = cnt_add(P, u, 1u);
-        // global donors of u
-        const int64_t uy = y + offy(own), ux = x + offx(own);
-        uint32_t need = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int64_t xn = ux + offx(k), yn = uy + offy(k);
-            if (xn < 0 || yn < 0 || xn >= P.nx || yn >= P.ny) continue;
-            const int64_t j = u + offi(k, P.nx);
-            need += (rd_rb(P, j) == (uint8_t)opp(k)) && gbit(P, j);
-        }
-        if (got != need) break;
-        __threadfence();
+        if (cnt_add_acq_rel(P, u, 1u) != kReadyAt) break;
         cur = u;
-        x = ux;
-        y = uy;
+        x += offx(own);
+        y += offy(own);
     }
     return n;
 }
 
-// Global phase of D8 forward routing: grid-stride over the global-cell list;
-// cells with no global dependency start walkers.  The last CTA to finish
-// checks that every cell of every problem was computed.
+// Global phase of D8 forward routing, first launch: every global cell's
+// arrival counter is preset to kReadyAt minus its number of global donors, and
+// the cells without global donors are listed (the walkers' starts, in the
+// frontier buffer).
+template <Mode M, bool W, bool AREA>
+__global__ void __launch_bounds__(256) k_global_init(const Prob* __restrict__ probs, Prob single,
+                                                     EngineGlobals* G) {
+    using E = Eng<M, W, AREA>;
+    const unsigned long long count = G->glist_count;
+    const Prob& P0 = probs ? probs[0] : single;
+    const unsigned long long* list = P0.glist;
+    unsigned long long* starts = reinterpret_cast<unsigned long long*>(P0.link);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long item = __ldcg(list + i);
+        const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+        const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
+        const uint32_t deps = g_deps_global<E>(P, cell);
+        if (deps) {
+            cnt_add(P, cell, kReadyAt - deps);
+        } else {
+            const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
+            if (FR_OK((int64_t)slot, P0.glist_cap, 18)) starts[slot] = item;
+        }
+    }
+}
+
+// Second launch: a walker from every start.  The last CTA to finish checks
+// that every cell of every problem was computed.
 template <Mode M, bool W, bool AREA>
 __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, Prob single,
                                                 EngineGlobals* G, unsigned long long total_cells) {
     using E = Eng<M, W, AREA>;
+    static_assert(E::kD8Fwd, "branching modes use k_global_levels");
     __shared__ unsigned long long s_done;
-    const unsigned long long count = G->glist_count;
-    const unsigned long long* list = probs ? probs[0].glist : single.glist;
+    const unsigned long long count = G->fcount[0];
+    const Prob& P0 = probs ? probs[0] : single;
+    const unsigned long long* starts = reinterpret_cast<const unsigned long long*>(P0.link);
     unsigned long long done = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long item = __ldcg(list + i);
-        const int pid = (int)(item >> 40);
-        const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
-        const Prob& P = probs ? probs[pid] : single;
-        if (g_deps_global<E>(P, cell) != 0) continue;
-        static_assert(E::kD8Fwd, "branching modes use k_global_levels");
-        done += walker_d8<W, AREA>(P, cell);
+        const unsigned long long item = __ldcg(starts + i);
+        const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+        done += walker_d8<W, AREA>(P, (int64_t)(item & ((1ull << 40) - 1)));
     }
     for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
     if (threadIdx.x == 0) s_done = 0;
@@ -351,7 +378,6 @@ __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, 
 // bounded in time.
 
 constexpr unsigned long long kBarrierLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
-constexpr uint32_t kReadyAt = 16u;  // > 8 dependencies, < 256 (one counter byte)
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -502,6 +528,9 @@ template <Mode M, bool W, bool AREA>
 cudaError_t launch_global(const Prob* probs, const Prob& single, EngineGlobals* G,
                           unsigned long long total_cells, cudaStream_t s) {
     if constexpr (M == Mode::FwdD8) {
+        k_global_init<M, W, AREA><<<walker_grid(), 256, 0, s>>>(probs, single, G);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         k_global<M, W, AREA><<<walker_grid(), 256, 0, s>>>(probs, single, G, total_cells);
         return cudaGetLastError();
     } else {
