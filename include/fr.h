@@ -73,6 +73,17 @@ typedef enum {
  *   FR_D4          D8 routing only (rejected for MFD): consider the four
  *                  orthogonal neighbours E N W S alone, the D4 scheme that
  *                  Sec. 2.1 names beside D8.
+ *   FR_DINF        MFD routing only (rejected for D8): Tarboton's D-infinity
+ *                  split, the other multiple-flow-direction scheme App. A
+ *                  names, instead of the slope-power split (p is then unused).
+ *                  Water goes down the steepest of the eight triangular facets
+ *                  (cell, cardinal neighbour, the diagonal next to it), chosen in
+ *                  fp32 on squared slopes (s1 = fl(fl(z - z_card) / dx),
+ *                  s2 = fl(fl(z_card - z_diag) / dx); along the cardinal if
+ *                  s2 <= 0, along the diagonal if s2 >= s1, else inside the
+ *                  facet), first facet on ties, and is split f_diag =
+ *                  atan2(s2, s1) / (pi/4), f_card = atan2(s1 - s2, s1 + s2) / (pi/4).
+ *                  dL/dz of the adjoint is not available for it.
  *   FR_CHECK_FINITE reject a DEM holding NaN or Inf (FR_ERR_NONFINITE; this
  *                  check synchronises the stream).
  */
@@ -82,6 +93,7 @@ typedef enum {
 #define FR_D8_LOWEST 0x2u
 #define FR_CHECK_FINITE 0x4u
 #define FR_D4 0x8u
+#define FR_DINF 0x10u
 
 #define FR_SINK 0xFFu
 

@@ -48,6 +48,7 @@ EDGE_ROUTE = 1
 D8_STEEPEST = 0
 D8_LOWEST = 2
 D4 = 8
+DINF = 16
 
 OFFX = (1, 0, -1, 0, 1, -1, -1, 1)
 OFFY = (0, -1, 0, 1, -1, -1, 1, 1)

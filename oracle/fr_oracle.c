@@ -53,6 +53,7 @@
 #define OR_EDGE_ROUTE 1u
 #define OR_D8_LOWEST 2u
 #define OR_D4 8u
+#define OR_DINF 16u
 
 static const int OFFX[8] = {+1, 0, -1, 0, +1, -1, -1, +1};
 static const int OFFY[8] = {0, -1, 0, +1, -1, -1, +1, +1};
@@ -96,8 +97,78 @@ void or_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx, uint32_t
  * strictly lower neighbour, f_k = s_k^p / sum_j s_j^p, FP64.  frac is N x 8,
  * zero where neighbour k is not a receiver.  mask bit k set iff f_k is a
  * receiver. */
+/* D-infinity (Tarboton 1997) for one cell: the water goes down the steepest of
+ * the eight triangular facets spanned by the cell, a cardinal neighbour e1 and
+ * the diagonal neighbour e2 next to it, split between e1 and e2 by the angle
+ * of the steepest direction within the facet.  Facet i pairs cardinal code
+ * ((i + 1) / 2) mod 4 with diagonal code 4 + i / 2 (E-NE, N-NE, N-NW, W-NW,
+ * W-SW, S-SW, S-SE, E-SE); facets with a neighbour off the grid are skipped.
+ * The choice is made in fp32 on squared slopes, s1 = fl(fl(e0 - e1) c1) and
+ * s2 = fl(fl(e1 - e2) c1) with c1 = fl32(1/dx), so that it is defined
+ * bit-for-bit:
+ *   s2 <= 0:        along e1 only, key s1^2 (if s1 > 0)
+ *   s2 >= s1:       along e2 only, sd = fl(fl(e0 - e2) cd), cd = fl32(1/(sqrt2 dx)),
+ *                   key sd^2 (if sd > 0)
+ *   otherwise:      inside the facet, key s1^2 + s2^2;
+ * the largest key wins, the first facet on ties; no positive key: a sink.
+ * Inside a facet the fractions are exact functions of those slopes (FP64):
+ *   f(e2) = atan2(s2, s1) / (pi/4),  f(e1) = atan2(s1 - s2, s1 + s2) / (pi/4)
+ * (they sum to 1; the second form keeps f(e1) accurate where it is small). */
+static void dinf_cell(const double* z, int64_t nx, int64_t ny, double dx, int64_t x, int64_t y,
+                      uint8_t* mask, double* f) {
+    const float c1 = (float)(1.0 / dx), cd = (float)(1.0 / (sqrt(2.0) * dx));
+    const float e0 = (float)z[y * nx + x];
+    float best = -1.0f, b1 = 0.0f, b2 = 0.0f;
+    int bi = -1, bkind = 0;
+    for (int i = 0; i < 8; ++i) {
+        const int kc = ((i + 1) / 2) % 4, kd = 4 + i / 2;
+        const int64_t xc = x + OFFX[kc], yc = y + OFFY[kc], xd = x + OFFX[kd], yd = y + OFFY[kd];
+        if (xc < 0 || yc < 0 || xc >= nx || yc >= ny || xd < 0 || yd < 0 || xd >= nx || yd >= ny)
+            continue;
+        const float e1 = (float)z[yc * nx + xc], e2 = (float)z[yd * nx + xd];
+        const float s1 = (e0 - e1) * c1, s2 = (e1 - e2) * c1;
+        float key;
+        int kind;
+        if (s2 <= 0.0f) {
+            kind = 0;
+            key = s1 > 0.0f ? s1 * s1 : -1.0f;
+        } else if (s2 >= s1) {
+            kind = 2;
+            const float sd = (e0 - e2) * cd;
+            key = sd > 0.0f ? sd * sd : -1.0f;
+        } else {
+            kind = 1;
+            key = s1 * s1 + s2 * s2;
+        }
+        if (key > best) { best = key; bi = i; bkind = kind; b1 = s1; b2 = s2; }
+    }
+    *mask = 0;
+    for (int k = 0; k < 8; ++k) f[k] = 0.0;
+    if (bi < 0) return;
+    const int kc = ((bi + 1) / 2) % 4, kd = 4 + bi / 2;
+    const double q = 4.0 / 3.14159265358979323846;
+    if (bkind == 0) { f[kc] = 1.0; *mask = (uint8_t)(1u << kc); return; }
+    if (bkind == 2) { f[kd] = 1.0; *mask = (uint8_t)(1u << kd); return; }
+    f[kd] = atan2((double)b2, (double)b1) * q;
+    f[kc] = atan2((double)b1 - (double)b2, (double)b1 + (double)b2) * q;
+    *mask = (uint8_t)((1u << kc) | (1u << kd));
+}
+
 void or_receivers_mfd(const double* z, int64_t nx, int64_t ny, double dx, double p, uint32_t flags,
                       uint8_t* mask, double* frac) {
+    if (flags & OR_DINF) {
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t i = y * nx + x;
+                if (!(flags & OR_EDGE_ROUTE) && is_edge(x, y, nx, ny)) {
+                    mask[i] = 0;
+                    for (int k = 0; k < 8; ++k) frac[i * 8 + k] = 0.0;
+                    continue;
+                }
+                dinf_cell(z, nx, ny, dx, x, y, &mask[i], &frac[i * 8]);
+            }
+        return;
+    }
     for (int64_t y = 0; y < ny; ++y) {
         for (int64_t x = 0; x < nx; ++x) {
             int64_t i = y * nx + x;

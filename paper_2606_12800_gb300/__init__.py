@@ -8,10 +8,10 @@ mass-balance check, as hand-written sm_103a CUDA behind the C ABI of
 that ABI; see ``api`` for the tensor-level functions and ``_lib`` for the raw
 ctypes binding with the C names.
 """
-from ._lib import (FR_CHECK_FINITE, FR_D4, FR_D8_LOWEST, FR_D8_STEEPEST, FR_EDGE_ROUTE, FR_EDGE_SINK,
+from ._lib import (FR_CHECK_FINITE, FR_D4, FR_DINF, FR_D8_LOWEST, FR_D8_STEEPEST, FR_EDGE_ROUTE, FR_EDGE_SINK,
                    FR_SINK, FrError)
 
-__all__ = ["api", "inputs", "FR_CHECK_FINITE", "FR_D4", "FR_D8_LOWEST", "FR_D8_STEEPEST", "FR_EDGE_ROUTE",
+__all__ = ["api", "inputs", "FR_CHECK_FINITE", "FR_D4", "FR_DINF", "FR_D8_LOWEST", "FR_D8_STEEPEST", "FR_EDGE_ROUTE",
            "FR_EDGE_SINK", "FR_SINK", "FrError"]
 
 

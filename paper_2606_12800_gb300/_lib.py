@@ -29,6 +29,7 @@ FR_EDGE_ROUTE = 0x1
 FR_D8_STEEPEST = 0x0
 FR_D8_LOWEST = 0x2
 FR_D4 = 0x8
+FR_DINF = 0x10
 FR_CHECK_FINITE = 0x4
 FR_SINK = 0xFF
 

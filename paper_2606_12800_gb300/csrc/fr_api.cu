@@ -13,7 +13,7 @@ namespace {
 
 constexpr int64_t kMaxCells = (int64_t)1 << 40;
 constexpr int kMassBlocks = 1024;
-constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE | FR_D4;
+constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE | FR_D4 | FR_DINF;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -89,7 +89,7 @@ fr_status check_finite(const float* z, int64_t n, cudaStream_t s) {
 bool routing_ok(const fr_routing* R) {
     if (!R || R->reserved || R->reserved2) return false;
     if (!sizes_ok(R->nx, R->ny)) return false;
-    if (R->kind == FR_ROUTING_D8) return R->dir != nullptr;
+    if (R->kind == FR_ROUTING_D8) return R->dir != nullptr && !(R->flags & FR_DINF);
     if (R->kind == FR_ROUTING_MFD)
         return R->mask && R->dem && std::isfinite(R->dx) && R->dx > 0 && std::isfinite(R->p) &&
                R->p > 0 && R->p <= FR_MFD_MAX_P && (R->flags & ~kKnownFlags) == 0 &&
@@ -165,7 +165,7 @@ fr_status fr_get_status(const void* ws, size_t ws_bytes, void* stream) {
 fr_status fr_receivers_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
                           uint8_t* dir_out, uint8_t* indeg_out, void* stream) {
     if (!dem || !dir_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
-        (flags & ~kKnownFlags))
+        (flags & ~kKnownFlags) || (flags & FR_DINF))
         return FR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags & FR_CHECK_FINITE) {
@@ -223,7 +223,7 @@ fr_status accumulate_impl(const fr_routing* R, const float* rain, float* w_out, 
     EngineGlobals* G = reinterpret_cast<EngineGlobals*>(ws);
     if (!mfd) return cuda_status(launch_d8_forward(w_out != nullptr, area_out != nullptr, P, G, s));
     if (!fracs_ready) {
-        e = launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p,
+        e = launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p, R->flags,
                                  reinterpret_cast<float*>((char*)ws + L.frac), s);
         if (e != cudaSuccess) return FR_ERR_CUDA;
     }
@@ -254,7 +254,7 @@ fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float
     Prob P = base_prob(R, (char*)ws);
     P.init = rain;
     const Layout L = layout(n);
-    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p,
+    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p, R->flags,
                                     reinterpret_cast<float*>((char*)ws + L.frac), s) != cudaSuccess)
         return FR_ERR_CUDA;
     // two iterates (interleaved two-float) in the frontier and list regions
@@ -291,7 +291,8 @@ fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float
 fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
                       const float* rain, float* w_out, float* w_lo_out, uint64_t* area_out,
                       uint8_t* dir_out, void* ws, size_t ws_bytes, void* stream) {
-    if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || (flags & ~kKnownFlags))
+    if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || (flags & ~kKnownFlags) ||
+        (flags & FR_DINF))
         return FR_ERR_INVALID_ARG;
     if (!ws_ok(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
     uint8_t* dir = dir_out ? dir_out : reinterpret_cast<uint8_t*>((char*)ws + layout(nx * ny).rb);
@@ -340,6 +341,7 @@ fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_l
                            size_t ws_bytes, void* stream) {
     if (!routing_ok(R) || !w || !dLdr_out) return FR_ERR_INVALID_ARG;
     if (dLdz_out && R->kind != FR_ROUTING_MFD) return FR_ERR_INVALID_ARG;
+    if (dLdz_out && (R->flags & FR_DINF)) return FR_ERR_UNSUPPORTED;  // dL/dz: Freeman weights only
     const int64_t n = R->nx * R->ny;
     const bool mfd = R->kind == FR_ROUTING_MFD;
     if (!(mfd ? ws_ok_mfd(ws, ws_bytes, n) : ws_ok(ws, ws_bytes, n))) return FR_ERR_WORKSPACE;
@@ -352,7 +354,7 @@ fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_l
     P.lo_full = dLdz_out ? 1 : 0;  // the elevation gradient reads every trailing word
     const Layout L = layout(n);
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return FR_ERR_CUDA;
-    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p,
+    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p, R->flags,
                                     reinterpret_cast<float*>((char*)ws + L.frac), s) != cudaSuccess)
         return FR_ERR_CUDA;
     cudaError_t e = launch_adjoint(mfd, P, reinterpret_cast<EngineGlobals*>(ws), s);

@@ -220,7 +220,7 @@ extern "C" {
 
 size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_t kind,
                                uint32_t flags) {
-    if (!tiles_ok(tiles_host, ntiles, kind) || (flags & ~(FR_EDGE_ROUTE | FR_D8_LOWEST | FR_D4))) return 0;
+    if (!tiles_ok(tiles_host, ntiles, kind) || (flags & ~(FR_EDGE_ROUTE | FR_D8_LOWEST | FR_D4 | FR_DINF))) return 0;
     return batch_layout(tiles_host, ntiles, kind).total;
 }
 
@@ -229,9 +229,10 @@ fr_status fr_route_batch(const fr_tile* tiles_host, const fr_tile* tiles_dev, in
                          void* stream) {
     if (kind != FR_ROUTING_D8 && kind != FR_ROUTING_MFD) return FR_ERR_INVALID_ARG;
     if (!tiles_dev || !tiles_ok(tiles_host, ntiles, kind)) return FR_ERR_INVALID_ARG;
-    if (flags & ~(FR_EDGE_ROUTE | FR_D8_LOWEST | FR_D4)) return FR_ERR_INVALID_ARG;
+    if (flags & ~(FR_EDGE_ROUTE | FR_D8_LOWEST | FR_D4 | FR_DINF)) return FR_ERR_INVALID_ARG;
     if (kind == FR_ROUTING_MFD && (!(p > 0 && p <= FR_MFD_MAX_P) || (flags & FR_D4)))
         return FR_ERR_INVALID_ARG;
+    if (kind == FR_ROUTING_D8 && (flags & FR_DINF)) return FR_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < batch_layout(tiles_host, ntiles, kind).total)
         return FR_ERR_WORKSPACE;
     Tune t;

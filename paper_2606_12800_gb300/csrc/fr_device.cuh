@@ -17,6 +17,7 @@ constexpr uint8_t kSink = 0xFF;
 constexpr uint32_t kEdgeRoute = 0x1u;
 constexpr uint32_t kD8Lowest = 0x2u;
 constexpr uint32_t kD4 = 0x8u;
+constexpr uint32_t kDinf = 0x10u;
 
 // Offsets as 2-bit fields (offset + 1) packed per code, decoded with plain
 // signed integer arithmetic (a nested-ternary form of these functions was
@@ -264,6 +265,63 @@ __device__ __forceinline__ void mfd_fracs8(float zc, const float (&zn)[8], uint3
     const df inv = m ? df_recip(df_tree8(t)) : df_make(0.0f);
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] = ((m >> k) & 1u) ? mfd_frac(u[k], inv).hi : 0.0f;
+}
+
+// D-infinity (Tarboton) receivers and fractions of one cell: the steepest of
+// the eight triangular facets (cell, cardinal neighbour kc, the diagonal kd
+// next to it; facet i: kc = ((i + 1) / 2) mod 4, kd = 4 + i / 2), chosen in
+// fp32 on squared slopes with the same rounded operations as the oracle, then
+// the split between kc and kd by the angle inside the facet:
+//   f(kd) = atan2(s2, s1) / (pi/4),  f(kc) = atan2(s1 - s2, s1 + s2) / (pi/4)
+// (s1 - s2 is exact in fp32 where f(kc) is small, s2 >= s1 / 2).  gm: the
+// in-grid neighbours.  Returns the receiver mask.
+__device__ __forceinline__ uint32_t dinf_cell(float zc, const float (&zn)[8], uint32_t gm,
+                                              float c1, float cd, float (&f)[8]) {
+    float best = -1.0f, b1 = 0.0f, b2 = 0.0f;
+    int bi = -1, bkind = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int kc = ((i + 1) >> 1) & 3, kd = 4 + (i >> 1);
+        if (!((gm >> kc) & 1u) || !((gm >> kd) & 1u)) continue;
+        const float s1 = __fmul_rn(__fsub_rn(zc, zn[kc]), c1);
+        const float s2 = __fmul_rn(__fsub_rn(zn[kc], zn[kd]), c1);
+        float key;
+        int kind;
+        if (s2 <= 0.0f) {
+            kind = 0;
+            key = s1 > 0.0f ? __fmul_rn(s1, s1) : -1.0f;
+        } else if (s2 >= s1) {
+            kind = 2;
+            const float sd = __fmul_rn(__fsub_rn(zc, zn[kd]), cd);
+            key = sd > 0.0f ? __fmul_rn(sd, sd) : -1.0f;
+        } else {
+            kind = 1;
+            key = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(s2, s2));
+        }
+        if (key > best) {
+            best = key;
+            bi = i;
+            bkind = kind;
+            b1 = s1;
+            b2 = s2;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = 0.0f;
+    if (bi < 0) return 0u;
+    const int kc = ((bi + 1) >> 1) & 3, kd = 4 + (bi >> 1);
+    if (bkind == 0) {
+        f[kc] = 1.0f;
+        return 1u << kc;
+    }
+    if (bkind == 2) {
+        f[kd] = 1.0f;
+        return 1u << kd;
+    }
+    constexpr float q = 1.27323954473516268615f;  // 4 / pi
+    f[kd] = __fmul_rn(atan2f(b2, b1), q);
+    f[kc] = __fmul_rn(atan2f(__fsub_rn(b1, b2), __fadd_rn(b1, b2)), q);
+    return (1u << kc) | (1u << kd);
 }
 
 // ------------------------------------------------------------ byte counters

@@ -94,7 +94,7 @@ cudaError_t richardson_sweep(bool mfd, const Prob& P, const float2* prev, float2
                              unsigned long long* counts, cudaStream_t s);
 cudaError_t richardson_output(const float2* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 cudaError_t launch_mfd_fractions(const float* z, const uint8_t* mask, int64_t nx, int64_t ny,
-                                 double dx, double p, float* frac, cudaStream_t s);
+                                 double dx, double p, uint32_t flags, float* frac, cudaStream_t s);
 cudaError_t launch_receivers_batch(int kind, const Prob* probs, const int64_t* prefix, int nprob,
                                    uint32_t flags, EngineGlobals* G, int grid, cudaStream_t s);
 

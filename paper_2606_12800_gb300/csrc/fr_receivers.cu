@@ -172,9 +172,16 @@ __device__ __forceinline__ void recv_mfd_tile(const float* __restrict__ z, int64
         if (gx >= 0 && gy >= 0 && gx < nx && gy < ny &&
             (edge_route || !is_edge(gx, gy, nx, ny))) {
             float zc = zs[(ry + 1) * HX + (rx + 1)];
+            if (flags & kDinf) {
+                float zn[8], f[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (zs[(ry + 1 + offy(k)) * HX + (rx + 1 + offx(k))] < zc) m |= (uint8_t)(1u << k);
+                for (int k = 0; k < 8; ++k) zn[k] = zs[(ry + 1 + offy(k)) * HX + (rx + 1 + offx(k))];
+                m = (uint8_t)dinf_cell(zc, zn, grid_mask8(gx, gy, nx, ny), mc.co_hi, mc.cd_hi, f);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (zs[(ry + 1 + offy(k)) * HX + (rx + 1 + offx(k))] < zc) m |= (uint8_t)(1u << k);
+            }
         }
         ms[ry * RX + rx] = m;
     }
@@ -191,7 +198,15 @@ __device__ __forceinline__ void recv_mfd_tile(const float* __restrict__ z, int64
             float zn[8], f[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) zn[k] = zs[(ly + 2 + offy(k)) * HX + (lx + 2 + offx(k))];
-            mfd_fracs8(zs[(ly + 2) * HX + (lx + 2)], zn, m, mc, f);
+            if (flags & kDinf) {
+                if (m) dinf_cell(zs[(ly + 2) * HX + (lx + 2)], zn, grid_mask8(gx, gy, nx, ny), mc.co_hi,
+                                 mc.cd_hi, f);
+                else
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) f[k] = 0.0f;
+            } else {
+                mfd_fracs8(zs[(ly + 2) * HX + (lx + 2)], zn, m, mc, f);
+            }
             float4* fo = reinterpret_cast<float4*>(frac + gi * 8);
             fo[0] = make_float4(f[0], f[1], f[2], f[3]);
             fo[1] = make_float4(f[4], f[5], f[6], f[7]);
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(RNT) k_receivers_mfd(const float* __restrict__
 __global__ void __launch_bounds__(RNT) k_mfd_fractions(const float* __restrict__ z,
                                                        const uint8_t* __restrict__ mask,
                                                        int64_t nx, int64_t ny, MfdConst mc,
-                                                       float* __restrict__ frac) {
+                                                       uint32_t flags, float* __restrict__ frac) {
     __shared__ float zs[HX * HY];
     int64_t x0, y0;
     tile_origin(nx, x0, y0);
@@ -238,7 +253,16 @@ __global__ void __launch_bounds__(RNT) k_mfd_fractions(const float* __restrict__
         float zn[8], f[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) zn[k] = zs[(ly + 2 + offy(k)) * HX + (lx + 2 + offx(k))];
-        mfd_fracs8(zs[(ly + 2) * HX + (lx + 2)], zn, m, mc, f);
+        if (flags & kDinf) {
+            // the D-infinity split of this cell (its receivers are the mask's)
+            if (m) dinf_cell(zs[(ly + 2) * HX + (lx + 2)], zn, grid_mask8(gx, gy, nx, ny), mc.co_hi,
+                             mc.cd_hi, f);
+            else
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k] = 0.0f;
+        } else {
+            mfd_fracs8(zs[(ly + 2) * HX + (lx + 2)], zn, m, mc, f);
+        }
         float4* fo = reinterpret_cast<float4*>(frac + gi * 8);
         fo[0] = make_float4(f[0], f[1], f[2], f[3]);
         fo[1] = make_float4(f[4], f[5], f[6], f[7]);
@@ -329,9 +353,9 @@ cudaError_t launch_receivers_mfd(const float* z, int64_t nx, int64_t ny, double 
 }
 
 cudaError_t launch_mfd_fractions(const float* z, const uint8_t* mask, int64_t nx, int64_t ny,
-                                 double dx, double p, float* frac, cudaStream_t s) {
+                                 double dx, double p, uint32_t flags, float* frac, cudaStream_t s) {
     const unsigned grid = (unsigned)(((nx + RTX - 1) / RTX) * ((ny + RTY - 1) / RTY));
-    k_mfd_fractions<<<grid, RNT, 0, s>>>(z, mask, nx, ny, make_mfd_const(dx, p), frac);
+    k_mfd_fractions<<<grid, RNT, 0, s>>>(z, mask, nx, ny, make_mfd_const(dx, p), flags, frac);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,8 @@ def test_argument_validation_is_synchronous(lib):
     # D4 is a D8-only rule
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 1.1, _lib.FR_D4, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_workspace_size(_lib.FR_OP_ROUTE, 4, 4, _lib.FR_D4) > 0
+    # D-infinity is an MFD-only split
+    assert lib.fr_receivers_d8(fake, 4, 4, 1.0, _lib.FR_DINF, fake, None, None) == _lib.FR_ERR_INVALID_ARG
     # fractions need 16-byte alignment
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 1.1, 0, fake, P(0x1004), None, None) == _lib.FR_ERR_INVALID_ARG
     R = _lib.fr_routing()

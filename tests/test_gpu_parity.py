@@ -100,7 +100,7 @@ def test_unit_rain_only_and_determinism(api):
 
 
 @pytest.mark.parametrize("shape", [(1, 9), (3, 3), (33, 65), (97, 131), (256, 256), (300, 517)])
-@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE])
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE, oracle.DINF, oracle.DINF | oracle.EDGE_ROUTE])
 def test_receivers_mfd(api, shape, flags):
     ny, nx = shape
     z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=ny + nx)
@@ -116,7 +116,7 @@ def test_receivers_mfd(api, shape, flags):
 
 
 @pytest.mark.parametrize("shape", [(1, 9), (33, 65), (97, 131), (256, 256), (300, 517)])
-@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE])
+@pytest.mark.parametrize("flags", [0, oracle.EDGE_ROUTE, oracle.DINF])
 def test_route_mfd_parity(api, shape, flags):
     ny, nx = shape
     z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=2 * ny + nx)
@@ -442,6 +442,37 @@ def test_route_batch_mfd(api):
     assert api.batch_status(outs) == 0
     for z, r, o in zip(dems, rains, outs):
         m_ref, f_ref, w_ref, _ = oracle.route_mfd(z, 30.0, 1.1, r)
+        np.testing.assert_array_equal(o["route"].cpu().numpy(), m_ref)
+        assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+def test_dinf_batch_adjoint_and_large_route(api):
+    """D-infinity through every MFD path: a 1024x1536 route (walkers), the
+    batched route, and the adjoint dL/drain; dL/dz is refused."""
+    ny, nx = 1024, 1536
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=77)
+    rain = inputs.rain_field(ny, nx, 77)
+    out = api.route_mfd(cuda(z), 30.0, 1.1, cuda(rain), oracle.DINF, want_lo=True, want_mask=True)
+    assert api.get_status() == 0
+    m_ref, f_ref, w_ref, order = oracle.route_mfd(z, 30.0, 1.1, rain, oracle.DINF)
+    np.testing.assert_array_equal(out["mask"].cpu().numpy(), m_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    zt = cuda(z)
+    R = api.routing_mfd(out["mask"].cuda(), zt, 30.0, 1.1, oracle.DINF)
+    wd, wl = out["w"].cuda(), out["w_lo"].cuda()
+    dLdr, _ = api.adjoint(R, wd, wl)
+    g_ref = oracle.adjoint(order, w_ref, frac=f_ref)
+    assert relerr(dLdr.cpu().numpy(), g_ref) <= RTOL_W
+    with pytest.raises(Exception):
+        api.adjoint(R, wd, wl, want_dz=True)
+    specs = _batch_specs()
+    dems = [inputs.fractal_dem(a, b, beta=c, tilt=0.0, seed=30 + i) for i, (a, b, c) in enumerate(specs)]
+    rains = [inputs.rain_field(d.shape[0], d.shape[1], i) for i, d in enumerate(dems)]
+    outs = api.route_batch([cuda(d) for d in dems], [cuda(r) for r in rains], "mfd", p=1.1,
+                           flags=oracle.DINF, want_w=True)
+    assert api.batch_status(outs) == 0
+    for d, r, o in zip(dems, rains, outs):
+        m_ref, _, w_ref, _ = oracle.route_mfd(d, 30.0, 1.1, r, oracle.DINF)
         np.testing.assert_array_equal(o["route"].cpu().numpy(), m_ref)
         assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
 

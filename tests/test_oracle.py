@@ -463,3 +463,51 @@ def test_d4_dense_solve_and_codes(seed):
     w, _ = oracle.accumulate_d8(d, order, rain)
     ref = np.linalg.solve(_dense_A_d8(d), rain.astype(np.float64).ravel())
     np.testing.assert_allclose(w.ravel(), ref, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ D-inf ----
+
+@pytest.mark.parametrize("a,b,want", [
+    (4.0, 1.0, {0: np.arctan2(3.0, 5.0) / (np.pi / 4), 7: np.arctan2(1.0, 4.0) / (np.pi / 4)}),
+    (2.0, 2.0, {7: 1.0}),     # along the diagonal: all to SE
+    (3.0, 0.0, {0: 1.0}),     # along x: all to E (first of the two tied facets)
+    (1.0, 4.0, {3: np.arctan2(3.0, 5.0) / (np.pi / 4), 7: np.arctan2(1.0, 4.0) / (np.pi / 4)}),
+])
+def test_dinf_plane_closed_form(a, b, want):
+    """z = 1000 - a x - b y (dx = 1): the steepest facet follows the gradient;
+    the water splits between its cardinal and diagonal neighbours in
+    proportion to the angle: f_diag = atan(min/max) / (pi/4)."""
+    ny, nx = 6, 7
+    y, x = np.mgrid[0:ny, 0:nx]
+    z = (1000.0 - a * x - b * y).astype(np.float32)
+    m, f = oracle.receivers_mfd(z.astype(np.float64), 1.0, 1.1, oracle.DINF)
+    for yy in range(1, ny - 1):
+        for xx in range(1, nx - 1):
+            assert m[yy, xx] == sum(1 << k for k in want)
+            for k in range(8):
+                assert f[yy, xx, k] == pytest.approx(want.get(k, 0.0), rel=1e-14, abs=1e-15)
+    assert (m[0, :] == 0).all() and (m[:, 0] == 0).all()  # edge cells are sinks
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_dinf_invariants_and_dense_solve(seed):
+    ny, nx = 19, 22
+    z = _dem(ny, nx, seed, beta=2.2, tilt=0.0).astype(np.float64)
+    rain = inputs.rain_field(ny, nx, seed)
+    m, f = oracle.receivers_mfd(z, 30.0, 1.1, oracle.DINF)
+    for yy in range(ny):
+        for xx in range(nx):
+            bits = [k for k in range(8) if (m[yy, xx] >> k) & 1]
+            assert len(bits) <= 2
+            if len(bits) == 2:
+                kc, kd = bits  # a cardinal and the diagonal next to it
+                assert kc < 4 <= kd and kd in (4 + ((kc * 2 - 1) % 8) // 2, 4 + (kc * 2) // 2 % 4)
+            for k in bits:
+                assert z[yy + OFFY[k], xx + OFFX[k]] < z[yy, xx]
+            if bits:
+                assert f[yy, xx].sum() == pytest.approx(1.0, abs=1e-14)
+            assert all(f[yy, xx, k] == 0.0 for k in range(8) if k not in bits)
+    order = oracle.high_to_low_order(z)
+    w = oracle.accumulate_mfd(f, order, rain)
+    ref = np.linalg.solve(_dense_A_mfd(f), rain.astype(np.float64).ravel())
+    np.testing.assert_allclose(w.ravel(), ref, rtol=1e-12)
