@@ -57,6 +57,7 @@ def routing_d8(dir_: torch.Tensor) -> fr_routing:
     R.kind = FR_ROUTING_D8
     R.ny, R.nx = dir_.shape
     R.dir = dir_.data_ptr()
+    R._keep = (dir_,)  # the descriptor holds raw pointers: keep the tensors alive
     return R
 
 
@@ -69,6 +70,7 @@ def routing_mfd(mask: torch.Tensor, dem: torch.Tensor, dx: float, p: float, flag
     R.dx = dx
     R.p = p
     R.flags = flags
+    R._keep = (mask, dem)
     return R
 
 

@@ -207,6 +207,54 @@ def test_cycle_reports_no_progress(api):
     assert api.get_status() == 0
 
 
+def _pit_lattice(ny, nx):
+    """3 x 3 blocks whose eight outer cells all drain into the centre (a sink):
+    every centre has eight donors, all of them leaves."""
+    d = np.full((ny, nx), oracle.SINK, np.uint8)
+    to_centre = {(-1, -1): 7, (-1, 0): 3, (-1, 1): 6, (0, -1): 0, (0, 1): 2,
+                 (1, -1): 4, (1, 0): 1, (1, 1): 5}  # code of the cell at (dy, dx) from the centre
+    for cy in range(1, ny - 1, 3):
+        for cx in range(1, nx - 1, 3):
+            for (dy, dx), k in to_centre.items():
+                d[cy + dy, cx + dx] = k
+    return d
+
+
+@pytest.mark.parametrize("shape", [(64, 96), (301, 517)])
+def test_eight_donor_cells(api, shape):
+    """Cells with eight donors are completed exactly once, whatever the order of
+    the donors' arrivals and of the cell's own count (repeated launches, both
+    tile geometries through the batched route)."""
+    ny, nx = shape
+    d = _pit_lattice(ny, nx)
+    rain = inputs.rain_field(ny, nx, 21)
+    w_ref, a_ref = oracle.accumulate_d8(d, oracle.kahn_order(d, False), rain)
+    assert a_ref.max() == 9
+    R = api.routing_d8(cuda(d))
+    rt = cuda(rain)
+    for _ in range(5):
+        o = api.accumulate(R, rt, want_w=True, want_area=True)
+        assert api.get_status() == 0
+        np.testing.assert_array_equal(o["area"].cpu().numpy().astype(np.uint64), a_ref)
+        assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
+    # the batched route with each tile geometry, from a DEM whose D8 codes are
+    # the lattice's: each block a cone falling towards its centre
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    cy, cx = 1 + 3 * ((yy - 1) // 3).clip(0), 1 + 3 * ((xx - 1) // 3).clip(0)
+    z = (np.maximum(np.abs(yy - cy), np.abs(xx - cx)) + 0.25 * (np.abs(yy - cy) + np.abs(xx - cx))
+         + 10.0).astype(np.float32)
+    d_z = oracle.receivers_d8(z, 30.0)
+    w_z, a_z = oracle.accumulate_d8(d_z, oracle.kahn_order(d_z, False), rain)
+    for _ in range(3):
+        outs = api.route_batch([cuda(z)] * 4, [rt] * 4, "d8", want_w=True, want_area=True,
+                               autotune=True)
+        assert api.batch_status(outs) == 0
+        for o in outs:
+            np.testing.assert_array_equal(o["route"].cpu().numpy(), d_z)
+            np.testing.assert_array_equal(o["area"].cpu().numpy().astype(np.uint64), a_z)
+            assert relerr(o["w"].cpu().numpy(), w_z) <= RTOL_W
+
+
 def test_routing_pointing_outside_grid_is_a_sink(api):
     """Caller-supplied codes that point out of the grid act as no receiver."""
     ny, nx = 16, 16
