@@ -1,0 +1,49 @@
+"""Named workloads run through the public API, for profiling one kernel at a
+chosen size (``ncu -k ...  python -m paper_2606_12800_gb300.cases mfd --n 4096``).
+
+Cases (all on seeded synthetic fractal DEMs, inputs resident on the device):
+  d8        receivers + D8 accumulation with rain U[0,1) (two-float w, uint64 areas)
+  d8_area   receivers + D8 unit-rain areas only
+  mfd       slope-split route (p = 1.1), unit rain
+  adjoint   slope-split route, then the adjoint of L = sum over sinks of w^2
+            (dL/drain and dL/dz)
+Each case runs ``--reps`` times and prints the device status word.
+"""
+import argparse
+
+import torch
+
+from . import api, inputs
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("case", choices=["d8", "d8_area", "mfd", "adjoint"])
+    ap.add_argument("--n", type=int, default=4096, help="grid side (n x n)")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1)
+    a = ap.parse_args(argv)
+    n, dev = a.n, torch.device("cuda", torch.cuda.current_device())
+    if a.case.startswith("d8"):
+        z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.01, seed=a.seed, device="cuda")
+        rain = None if a.case == "d8_area" else inputs.rain_field_torch(n, n, a.seed, device="cuda")
+        d = api.receivers_d8(z, 30.0)
+        R = api.routing_d8(d)
+        for _ in range(a.reps):
+            api.receivers_d8(z, 30.0)
+            api.accumulate(R, rain, want_w=rain is not None, want_area=True, device=dev)
+    else:
+        z = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=a.seed, device="cuda")
+        for _ in range(a.reps):
+            out = api.route_mfd(z, 30.0, 1.1, None, 0, want_lo=True, want_mask=True)
+            if a.case == "adjoint":
+                R = api.routing_mfd(out["mask"], z, 30.0, 1.1)
+                api.adjoint(R, out["w"], out["w_lo"], want_dz=True)
+    torch.cuda.synchronize()
+    st = api.get_status(dev)
+    print("case %s n=%d reps=%d status %d" % (a.case, n, a.reps, st))
+    return 0 if st == 0 else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
