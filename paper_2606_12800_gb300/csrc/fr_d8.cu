@@ -76,6 +76,27 @@ struct SmemD8 {
     unsigned long long done;
 };
 
+// Warp-aggregated append of four optional cells per lane (-1: none; all lanes
+// call): one ballot per slot, one atomic per warp.
+template <class S_>
+__device__ __forceinline__ void push4(S_& S, const int (&cq)[4]) {
+    const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
+    int prefix = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned b = __ballot_sync(0xffffffffu, cq[q] >= 0);
+        prefix += __popc(b & below);
+        total += __popc(b);
+    }
+    if (!total) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&S.qtail, total);
+    int pos = __shfl_sync(0xffffffffu, base, 0) + prefix;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (cq[q] >= 0) S.queue[pos++] = (uint16_t)cq[q];
+}
+
 // Warp-aggregated append of up to four starts per lane (all lanes call).
 template <class S_>
 __device__ __forceinline__ void push_starts(S_& S, int n, const int (&cells)[4]) {
@@ -226,8 +247,7 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
         // arrival came last) goes to the ready list.
         for (int gq0 = 0; gq0 < NE / 4; gq0 += NT8) {
             const int gq = gq0 + tid;
-            int cells[4];
-            int n = 0;
+            int cq[4] = {-1, -1, -1, -1};  // cells completed in this pass (one per slot)
             if (gq < NE / 4) {
                 const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
                 const int w1 = (ex + 4) >> 2;
@@ -252,17 +272,17 @@ __global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
                     const uint32_t old = atomicAdd(&S.pk[r + q], pre);
                     if (((old + pre) >> 20) != kPkDone) continue;
                     if (d) {
-                        cells[n++] = r + q;  // the last donor arrived before the preset
+                        cq[q] = r + q;  // the last donor arrived before the preset
                         continue;
                     }
                     const uint32_t k = (mid.c >> (8 * q)) & 0xFFu;  // a leaf: arrive now
                     if (k >= 8) continue;
                     const int t = r + q + offy((int)k) * CP + offx((int)k);
                     const uint32_t add = kPkArrive | 1u;
-                    if (((atomicAdd(&S.pk[t], add) + add) >> 20) == kPkDone) cells[n++] = t;
+                    if (((atomicAdd(&S.pk[t], add) + add) >> 20) == kPkDone) cq[q] = t;
                 }
             }
-            push_starts(S, n, cells);
+            push4(S, cq);
         }
     } else {
         // ---- scalar path (tiles touching the grid boundary)
