@@ -36,11 +36,11 @@ namespace fr {
 namespace {
 
 constexpr int D8H = 4;
-constexpr int NT8 = 512;
 
-template <int TX_, int TY_>
+template <int TX_, int TY_, int NT_ = 512>
 struct D8Geo {
     static constexpr int TX = TX_, TY = TY_, H = D8H;
+    static constexpr int NT = NT_;  // threads per CTA
     static constexpr int EX = TX + 2 * H, EY = TY + 2 * H, NE = EX * EY;  // extended region
     static constexpr int RY = EY + 2;  // region plus a one-cell ring
     static constexpr int CP = EX + 8;  // padded row pitch (bytes) of ring-sized byte arrays
@@ -183,11 +183,11 @@ __device__ __forceinline__ int batch_problem(const int64_t* __restrict__ prefix,
 }
 
 template <class Gm, bool W, bool AREA, bool BATCH>
-__global__ void __launch_bounds__(NT8) k_local_d8(Prob Pone, EngineGlobals* G,
+__global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G,
                                                   const Prob* __restrict__ probs,
                                                   const int64_t* __restrict__ prefix, int nprob) {
     constexpr int TX = Gm::TX, TY = Gm::TY, H = Gm::H, EX = Gm::EX, EY = Gm::EY, NE = Gm::NE;
-    constexpr int RY = Gm::RY, CP = Gm::CP;
+    constexpr int RY = Gm::RY, CP = Gm::CP, NT8 = Gm::NT;
     using Sm = SmemD8<Gm, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm& S = *reinterpret_cast<Sm*>(smem_raw);
@@ -482,7 +482,7 @@ cudaError_t launch_local_d8(const Prob& P, EngineGlobals* G, const Prob* probs,
     cudaError_t e = cudaFuncSetAttribute(k_local_d8<Gm, W, AREA, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    if (tiles > 0) k_local_d8<Gm, W, AREA, BATCH><<<(unsigned)tiles, NT8, sm, s>>>(P, G, probs, prefix, nprob);
+    if (tiles > 0) k_local_d8<Gm, W, AREA, BATCH><<<(unsigned)tiles, Gm::NT, sm, s>>>(P, G, probs, prefix, nprob);
     return cudaGetLastError();
 }
 
@@ -520,11 +520,13 @@ cudaError_t d8_batch_w(bool want_w, bool want_area, const Prob* probs, const int
 // D8 forward accumulation: halo-tile local phase + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& P, EngineGlobals* G,
                               cudaStream_t s) {
-    // 128x32 inner tiles: less halo per inner cell; measured fastest for the
-    // walker solve at 4096^2 (with rain) and 32768^2 (areas only)
+    // 128x32 inner tiles with values (two blocks of 95 KB per SM); areas alone
+    // need 5 bytes of shared memory per region cell, which leaves room for
+    // 128x64 tiles (1.20x halo redundancy instead of 1.33x, three blocks per
+    // SM).  Both measured fastest among 64x32 ... 128x96 for their case.
     if (want_w && want_area) return launch_d8<GeoD8, true, true>(P, G, s);
     if (want_w) return launch_d8<GeoD8, true, false>(P, G, s);
-    return launch_d8<GeoD8, false, true>(P, G, s);
+    return launch_d8<D8Geo<kD8TileX, 2 * kD8TileY>, false, true>(P, G, s);
 }
 
 // Batched D8 forward: the CTAs of all problems' tiles in one launch (tile
