@@ -9,11 +9,13 @@
 // of fr_engine.cuh then finishes.  Halo cells are solved only to feed the
 // inner ones and are not written.
 //
-// Solve: every cell waits for all its donors.  Walkers start at the cells
-// without donors; a walker finalises its cell and adds the cell's local area
-// to the receiver with one shared-memory atomic on a packed word (arrival
-// count, donors' area sum).  The donor that arrives last continues with the
-// receiver ("last arriver continues"), the others take their next start.  No
+// Solve: every cell waits for all its donors.  A cell's packed word (arrival
+// count, donors' area sum) starts at its preset; each donor, once final, adds
+// its local area with one shared-memory atomic.  The cells without donors
+// (leaves, two thirds of a rough DEM) are final at once and arrive in one
+// parallel pass; the receivers they complete form a list, and walkers drain
+// it: a walker finalises its cell, arrives at the receiver, and continues
+// with the receiver if it arrived last ("last arriver continues").  No
 // block barrier separates the cells of a chain, each cell is visited once, and
 // a cell's two-float value is pulled from its final donors in fixed code
 // order (deterministic sums; exact 16-bit local areas).  The visiting order
@@ -241,13 +243,17 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
         }
         cp_async_wait_all();
         __syncthreads();
-        // ---- donor masks, presets and the leaves' arrivals (four cells per
-        // thread step).  A leaf (no donors) is final at once and arrives at its
-        // receiver here; a cell completed in this pass (its preset or a leaf's
-        // arrival came last) goes to the ready list.
-        for (int gq0 = 0; gq0 < NE / 4; gq0 += NT8) {
-            const int gq = gq0 + tid;
-            int cq[4] = {-1, -1, -1, -1};  // cells completed in this pass (one per slot)
+        // ---- donor masks and presets (four cells per thread step, plain
+        // stores); the leaves (no donors: final at once) and their receivers'
+        // codes are kept in registers
+        constexpr int NG = (NE / 4 + NT8 - 1) / NT8;
+        static_assert(4 * NG <= 32, "leaf bits of a thread fit one word");
+        uint32_t leaves = 0;       // bit 4 * it + q
+        uint32_t lcode[NG];        // the four codes of group it
+#pragma unroll
+        for (int it = 0; it < NG; ++it) {
+            const int gq = it * NT8 + tid;
+            lcode[it] = 0;
             if (gq < NE / 4) {
                 const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
                 const int w1 = (ex + 4) >> 2;
@@ -258,25 +264,36 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     dmf |= zero_bytes(nbr(up, mid, dn, k) ^ (0x01010101u * (uint32_t)opp(k))) >> (7 - k);
-                const uint32_t cnt = popc_bytes(dmf);
+                const uint32_t wait = 0x09090909u - popc_bytes(dmf);  // kPkDone - donors
                 const int r = (ey + 1) * CP + ex + 4;
+                *reinterpret_cast<uint4*>(S.pk + r) =
+                    make_uint4((wait & 0xFFu) << 20, ((wait >> 8) & 0xFFu) << 20,
+                               ((wait >> 16) & 0xFFu) << 20, (wait >> 24) << 20);
                 if constexpr (W) {
                     *reinterpret_cast<uint32_t*>(S.dm + r) = dmf;
                     if (!P.init) *reinterpret_cast<float4*>(S.vhi + r) = make_float4(1.f, 1.f, 1.f, 1.f);
                     *reinterpret_cast<float4*>(S.vlo + r) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+                const uint32_t z = zero_bytes(dmf);  // 0x80 per leaf
+                leaves |= (((z >> 7) & 1u) | ((z >> 14) & 2u) | ((z >> 21) & 4u) | ((z >> 28) & 8u)) << (4 * it);
+                lcode[it] = mid.c;
+            }
+        }
+        __syncthreads();
+        // ---- the leaves arrive at their receivers; a receiver completed here
+        // (its last donor was a leaf) goes to the ready list
+#pragma unroll
+        for (int it = 0; it < NG; ++it) {
+            const int gq = it * NT8 + tid;
+            int cq[4] = {-1, -1, -1, -1};
+            const uint32_t lb = (leaves >> (4 * it)) & 0xFu;
+            if (lb) {
+                const int ey = gq / (EX / 4), ex = (gq - ey * (EX / 4)) * 4;
+                const int r = (ey + 1) * CP + ex + 4;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const uint32_t d = (cnt >> (8 * q)) & 0xFFu;
-                    const uint32_t pre = (kPkDone - d) << 20;
-                    const uint32_t old = atomicAdd(&S.pk[r + q], pre);
-                    if (((old + pre) >> 20) != kPkDone) continue;
-                    if (d) {
-                        cq[q] = r + q;  // the last donor arrived before the preset
-                        continue;
-                    }
-                    const uint32_t k = (mid.c >> (8 * q)) & 0xFFu;  // a leaf: arrive now
-                    if (k >= 8) continue;
+                    const uint32_t k = (lcode[it] >> (8 * q)) & 0xFFu;
+                    if (!((lb >> q) & 1u) || k >= 8) continue;
                     const int t = r + q + offy((int)k) * CP + offx((int)k);
                     const uint32_t add = kPkArrive | 1u;
                     if (((atomicAdd(&S.pk[t], add) + add) >> 20) == kPkDone) cq[q] = t;
