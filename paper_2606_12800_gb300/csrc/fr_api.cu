@@ -18,10 +18,11 @@ constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Workspace layout (same for every operation on an nx*ny grid):
-//   globals (64 B) | arrival counters (1 B/cell) | global-cell bits (1 bit/cell)
+//   globals (128 B) | global-cell bits (1 bit/cell) | arrival counters (1 B/cell)
 //   | trailing words (4 B/cell) | frontier buffer (8 B/cell)
 //   | global-cell list (8 B/cell) | routing bytes (1 B/cell) | mass partials
-// The first three regions are zeroed by each engine call (one memset).
+// The first two regions are zeroed by each engine call (one memset); a global
+// cell's arrival counter is stored before it is first counted.
 struct Layout {
     size_t cnt, gbits, lo, link, glist, rb, partials, total, zero_bytes;
     size_t frac, total_mfd;  // MFD only: fractions (32 B/cell) after the common part
@@ -30,11 +31,11 @@ struct Layout {
 Layout layout(int64_t n) {
     Layout L;
     size_t off = 256;
-    L.cnt = off;
-    off += align256((size_t)n + 4);
     L.gbits = off;
     off += align256(((size_t)n + 31) / 32 * 4);
     L.zero_bytes = off;
+    L.cnt = off;
+    off += align256((size_t)n + 4);
     L.lo = off;
     off += align256((size_t)n * 4);
     L.link = off;

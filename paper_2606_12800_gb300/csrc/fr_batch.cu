@@ -35,11 +35,11 @@ BatchLayout batch_layout(const fr_tile* t, int n, int kind = FR_ROUTING_D8, int 
         et += halo_tiles(kind == FR_ROUTING_MFD, geo, t[i].nx, t[i].ny);
     }
     size_t off = 256;
-    L.cnt = off;
-    off += a256((size_t)cb);
     L.gbits = off;
     off += a256((size_t)gw * 4);
-    L.zero_bytes = off;
+    L.zero_bytes = off;  // globals and global-cell bits; counters are stored before use
+    L.cnt = off;
+    off += a256((size_t)cb);
     L.lo = off;
     off += a256((size_t)cells * 4);
     L.link = off;

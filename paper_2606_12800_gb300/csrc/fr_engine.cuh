@@ -88,6 +88,12 @@ __device__ __forceinline__ uint64_t rd_area(const Prob& P, int64_t i) {
 __device__ __forceinline__ void wr_area(const Prob& P, int64_t i, uint64_t v) {
     if (FR_OK(i, ncell(P), 4)) P.area[i] = v;
 }
+// Stores cell i's counter (its preset), before any add to it: the init kernel
+// of the global phase or the first round, ahead of a launch or grid barrier.
+// Byte stores leave the neighbouring counters of the word alone.
+__device__ __forceinline__ void cnt_set(const Prob& P, int64_t i, uint32_t v) {
+    if (FR_OK(i, ncell(P), 5)) reinterpret_cast<uint8_t*>(P.cnt)[i] = (uint8_t)v;
+}
 __device__ __forceinline__ uint32_t cnt_add(const Prob& P, int64_t i, uint32_t n) {
     return FR_OK(i, ncell(P), 5) ? counter_add(P.cnt, i, n) : 0xFFu;
 }
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(256) k_global_init(const Prob* __restrict__ pr
         const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
         const uint32_t deps = g_deps_global<E>(P, cell);
         if (deps) {
-            cnt_add(P, cell, kReadyAt - deps);
+            cnt_set(P, cell, kReadyAt - deps);
         } else {
             const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
             if (FR_OK((int64_t)slot, P0.glist_cap, 18)) starts[slot] = item;
@@ -478,7 +484,7 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
         const int64_t cell = (int64_t)(item & kCellMask);
         const uint32_t deps = g_deps_global<E>(P, cell);
         if (deps) {
-            cnt_add(P, cell, kReadyAt - deps);
+            cnt_set(P, cell, kReadyAt - deps);
             continue;
         }
         const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
