@@ -213,11 +213,22 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
                      (!W || !P.init || ((uintptr_t)P.init & 15) == 0) &&
                      (!W || ((uintptr_t)P.out_hi & 15) == 0) &&
                      (!AREA || ((uintptr_t)P.area & 15) == 0);
-    // every packed word starts at zero; a region cell adds its preset (9 - donors)
-    // and each donor one arrival, in any order, and whichever add completes the
-    // count to 9 finalises the cell.  Ring cells get no preset and at most three
-    // arrivals, so they never finish.
-    for (int i = tid; i < Sm::NR / 4; i += NT8) reinterpret_cast<uint4*>(S.pk)[i] = make_uint4(0, 0, 0, 0);
+    // a region cell's packed word starts at its preset (9 - donors) and each donor
+    // adds one arrival; the add that completes the count to 9 finalises the cell.
+    // Ring cells start at zero and get at most three arrivals, so they never
+    // finish.  The vector path stores the presets after this barrier and zeroes
+    // only the ring here; the scalar path adds the presets atomically, in any
+    // order with the arrivals, onto a zeroed array.
+    if (vec) {
+        for (int i = tid; i < 2 * CP + 2 * EY; i += NT8) {
+            const int r = i < 2 * CP ? (i < CP ? i : (RY - 1) * CP + i - CP)
+                                     : (i - 2 * CP < EY ? (i - 2 * CP + 1) * CP + 3
+                                                        : (i - 2 * CP - EY + 1) * CP + EX + 4);
+            S.pk[r] = 0u;
+        }
+    } else {
+        for (int i = tid; i < Sm::NR / 4; i += NT8) reinterpret_cast<uint4*>(S.pk)[i] = make_uint4(0, 0, 0, 0);
+    }
     if (tid == 0) {
         S.qtail = 0;
         S.head = 0;

@@ -86,11 +86,16 @@ __device__ __forceinline__ void recv_d8_tile(const float* __restrict__ z, int64_
         uint32_t packed = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            // D4: the diagonals read +inf, which is never strictly lower
-            const float zn[8] = {w[1][q + 2], w[0][q + 1], w[1][q], w[2][q + 1],
-                                 d4 ? inf : w[0][q + 2], d4 ? inf : w[0][q],
-                                 d4 ? inf : w[2][q], d4 ? inf : w[2][q + 2]};
-            uint8_t code = (uint8_t)d8_code_sel<LOWEST>(w[1][q + 1], zn, c_orth, c_diag);
+            uint8_t code;
+            if (!d4) {  // uniform over the launch: the common path carries no selects
+                const float zn[8] = {w[1][q + 2], w[0][q + 1], w[1][q], w[2][q + 1],
+                                     w[0][q + 2], w[0][q], w[2][q], w[2][q + 2]};
+                code = (uint8_t)d8_code_sel<LOWEST>(w[1][q + 1], zn, c_orth, c_diag);
+            } else {
+                // D4: the diagonals read +inf, which is never strictly lower
+                const float zn[8] = {w[1][q + 2], w[0][q + 1], w[1][q], w[2][q + 1], inf, inf, inf, inf};
+                code = (uint8_t)d8_code_sel<LOWEST>(w[1][q + 1], zn, c_orth, c_diag);
+            }
             if (!interior) {  // interior tiles hold no edge cell and no cell off the grid
                 const int64_t gx = x0 + qx + q, gy = y0 + r;
                 if (gx >= nx || gy >= ny || (!edge_route && is_edge(gx, gy, nx, ny))) code = kSink;
