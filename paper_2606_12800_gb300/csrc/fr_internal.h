@@ -110,7 +110,7 @@ __host__ __device__ inline int64_t receiver_tiles(int64_t nx, int64_t ny) {
 constexpr int kD8TileX = 128;
 constexpr int kD8TileY = 32;
 constexpr int kMfdTileX = 64;
-constexpr int kMfdTileY = 32;
+constexpr int kMfdTileY = 64;  // 64x64 + 8 halo: 1.56x region cells per inner cell
 constexpr int kD8Geometries = 2;
 __host__ __device__ inline int64_t halo_tiles(int kind_mfd, int geo, int64_t nx, int64_t ny) {
     const int64_t tx = kind_mfd ? kMfdTileX : (geo == 1 ? kD8TileX / 2 : kD8TileX);
