@@ -548,12 +548,13 @@ cudaError_t d8_batch_w(bool want_w, bool want_area, const Prob* probs, const int
 // D8 forward accumulation: halo-tile local phase + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& P, EngineGlobals* G,
                               cudaStream_t s) {
-    // 128x32 inner tiles with values (two blocks of 95 KB per SM); areas alone
-    // need 5 bytes of shared memory per region cell, which leaves room for
-    // 128x64 tiles (1.20x halo redundancy instead of 1.33x, three blocks per
-    // SM).  Both measured fastest among 64x32 ... 128x96 for their case.
-    if (want_w && want_area) return launch_d8<GeoD8, true, true>(P, G, s);
-    if (want_w) return launch_d8<GeoD8, true, false>(P, G, s);
+    // With values a region cell needs 14 bytes of shared memory: 96x48 inner
+    // tiles (1.26x halo redundancy, two blocks of about 103 KB per SM).  Areas
+    // alone need 5 bytes, which leaves room for 128x64 tiles (1.20x, three
+    // blocks per SM).  Each measured fastest among 64x32 ... 128x96 for its
+    // case (with values: 128x32 and 64x64 were 5 % slower at 4096^2).
+    if (want_w && want_area) return launch_d8<D8Geo<96, 48>, true, true>(P, G, s);
+    if (want_w) return launch_d8<D8Geo<96, 48>, true, false>(P, G, s);
     return launch_d8<D8Geo<kD8TileX, 2 * kD8TileY>, false, true>(P, G, s);
 }
 
