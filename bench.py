@@ -41,7 +41,7 @@ SEED = 1
 # DRAM bytes (read + write) of one k_local_d8 launch on the 4096^2 workload, from
 # an ncu capture of this kernel as it stands (profiles/k_local_d8_4096.md);
 # None whenever the kernel changes until it is captured again.
-TRAFFIC_K_LOCAL_D8 = 90.648832e6 + 150.693120e6
+TRAFFIC_K_LOCAL_D8 = 88.336640e6 + 147.438336e6
 
 
 def parse():

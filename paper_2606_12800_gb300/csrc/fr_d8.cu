@@ -533,6 +533,7 @@ cudaError_t launch_d8_batch(const Prob* probs, const int64_t* prefix, int nprob,
 
 using GeoD8 = D8Geo<kD8TileX, kD8TileY>;        // geometry 0: 128x32
 using GeoD8s = D8Geo<kD8TileX / 2, kD8TileY>;   // geometry 1: 64x32
+using GeoD8w = D8Geo<96, 48>;                   // geometry 2: 96x48
 
 template <class Gm>
 cudaError_t d8_batch_w(bool want_w, bool want_area, const Prob* probs, const int64_t* prefix,
@@ -553,8 +554,8 @@ cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& P, Engine
     // alone need 5 bytes, which leaves room for 128x64 tiles (1.20x, three
     // blocks per SM).  Each measured fastest among 64x32 ... 128x96 for its
     // case (with values: 128x32 and 64x64 were 5 % slower at 4096^2).
-    if (want_w && want_area) return launch_d8<D8Geo<96, 48>, true, true>(P, G, s);
-    if (want_w) return launch_d8<D8Geo<96, 48>, true, false>(P, G, s);
+    if (want_w && want_area) return launch_d8<GeoD8w, true, true>(P, G, s);
+    if (want_w) return launch_d8<GeoD8w, true, false>(P, G, s);
     return launch_d8<D8Geo<kD8TileX, 2 * kD8TileY>, false, true>(P, G, s);
 }
 
@@ -564,6 +565,7 @@ cudaError_t launch_d8_forward_batch(int geo, bool want_w, bool want_area, const 
                                     const int64_t* prefix, int nprob, int64_t tiles,
                                     unsigned long long total_cells, EngineGlobals* G, cudaStream_t s) {
     if (geo == 1) return d8_batch_w<GeoD8s>(want_w, want_area, probs, prefix, nprob, tiles, total_cells, G, s);
+    if (geo == 2) return d8_batch_w<GeoD8w>(want_w, want_area, probs, prefix, nprob, tiles, total_cells, G, s);
     return d8_batch_w<GeoD8>(want_w, want_area, probs, prefix, nprob, tiles, total_cells, G, s);
 }
 

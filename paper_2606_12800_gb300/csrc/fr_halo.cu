@@ -1,8 +1,8 @@
 // fr_halo.cu -- local phase over halo-extended tiles for MFD (slope-split)
 // forward accumulation and for the adjoints of both routing rules.
 //
-// Same scheme as the D8 forward kernel: each CTA solves an inner tile plus an
-// H-cell halo exactly in shared memory (a per-subdomain high-to-low solve,
+// Same decomposition as the D8 forward kernel: each CTA solves an inner tile
+// plus an H-cell halo exactly in shared memory (a per-subdomain high-to-low solve,
 // Sec. 2.4, on overlapping subdomains), and only cells whose dependencies
 // reach outside the extended region go to the global phase.  With several
 // receivers per cell (App. A) dependency sets spread wider than D8 basins, so

@@ -106,15 +106,15 @@ __host__ __device__ inline int64_t receiver_tiles(int64_t nx, int64_t ny) {
 }
 
 // Inner tiles of the halo kernels: D8 geometry 0 is kD8TileX x kD8TileY,
-// geometry 1 half as wide; MFD uses kMfdTileX x kMfdTileY.
+// geometry 1 half as wide, geometry 2 is 96x48; MFD uses kMfdTileX x kMfdTileY.
 constexpr int kD8TileX = 128;
 constexpr int kD8TileY = 32;
 constexpr int kMfdTileX = 64;
 constexpr int kMfdTileY = 64;  // 64x64 + 8 halo: 1.56x region cells per inner cell
-constexpr int kD8Geometries = 2;
+constexpr int kD8Geometries = 3;
 __host__ __device__ inline int64_t halo_tiles(int kind_mfd, int geo, int64_t nx, int64_t ny) {
-    const int64_t tx = kind_mfd ? kMfdTileX : (geo == 1 ? kD8TileX / 2 : kD8TileX);
-    const int64_t ty = kind_mfd ? kMfdTileY : kD8TileY;
+    const int64_t tx = kind_mfd ? kMfdTileX : (geo == 1 ? kD8TileX / 2 : geo == 2 ? 96 : kD8TileX);
+    const int64_t ty = kind_mfd ? kMfdTileY : (geo == 2 ? 48 : kD8TileY);
     return ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
 }
 
