@@ -507,8 +507,8 @@ template <class Gm, bool W, bool AREA, bool BATCH>
 cudaError_t launch_local_d8(const Prob& P, EngineGlobals* G, const Prob* probs,
                             const int64_t* prefix, int nprob, int64_t tiles, cudaStream_t s) {
     constexpr size_t sm = sizeof(SmemD8<Gm, W>);
-    cudaError_t e = cudaFuncSetAttribute(k_local_d8<Gm, W, AREA, BATCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<unsigned long long> set_on{0};
+    cudaError_t e = smem_limit_once(k_local_d8<Gm, W, AREA, BATCH>, sm, set_on);
     if (e != cudaSuccess) return e;
     if (tiles > 0) k_local_d8<Gm, W, AREA, BATCH><<<(unsigned)tiles, Gm::NT, sm, s>>>(P, G, probs, prefix, nprob);
     return cudaGetLastError();

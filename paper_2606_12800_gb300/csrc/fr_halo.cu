@@ -350,8 +350,8 @@ template <Mode M, bool BATCH>
 cudaError_t launch_local_halo(const Prob& P, EngineGlobals* G, const Prob* probs,
                               const int64_t* prefix, int nprob, int64_t tiles, cudaStream_t s) {
     constexpr size_t sm = sizeof(SmemHalo);
-    cudaError_t e = cudaFuncSetAttribute(k_local_halo<M, BATCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<unsigned long long> set_on{0};
+    cudaError_t e = smem_limit_once(k_local_halo<M, BATCH>, sm, set_on);
     if (e != cudaSuccess) return e;
     if (tiles > 0) k_local_halo<M, BATCH><<<(unsigned)tiles, kHaloNT, sm, s>>>(P, G, probs, prefix, nprob);
     return cudaGetLastError();

@@ -1,6 +1,7 @@
 // fr_internal.h -- host-side interfaces between the translation units of libfr.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -116,6 +117,21 @@ __host__ __device__ inline int64_t halo_tiles(int kind_mfd, int geo, int64_t nx,
     const int64_t tx = kind_mfd ? kMfdTileX : (geo == 1 ? kD8TileX / 2 : geo == 2 ? 96 : kD8TileX);
     const int64_t ty = kind_mfd ? kMfdTileY : (geo == 2 ? 48 : kD8TileY);
     return ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+}
+
+// Raises a kernel's dynamic shared-memory limit once per device: the first
+// launch on each device sets the attribute, later launches skip the call
+// (`done` holds one bit per device; devices past 63 set it every time).
+template <class K>
+inline cudaError_t smem_limit_once(K kernel, size_t bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
 }
 
 }  // namespace fr
