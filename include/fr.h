@@ -170,8 +170,9 @@ typedef struct {
  * on; sinks keep their water.
  *   rain      [ny*nx] float32 >= 0, or NULL for unit rain (1 per cell).
  *   w_out     [ny*nx] float32 or NULL: water per cell, the leading word of a
- *             compensated two-float sum (error a few units in the last place
- *             of fp32 for D8; see the design notes for MFD).
+ *             compensated two-float sum (relative error against an FP64 solve
+ *             about 1e-7 for D8 and MFD: the rounding of the leading word, plus
+ *             the fp32 fractions for MFD).
  *   w_lo_out  [ny*nx] float32 or NULL: trailing word of that sum
  *             (w ~= w_out + w_lo_out).
  *   area_out  [ny*nx] uint64 or NULL: D8 only -- unit-rain drainage area in
@@ -309,7 +310,8 @@ typedef struct {
  * no host memory when it executes and can be captured in a CUDA graph.  All
  * tiles must request the same outputs (w_out / area_out set for all or none;
  * area_out only with FR_ROUTING_D8, w_out required with FR_ROUTING_MFD).
- * flags: FR_EDGE_* and FR_D8_* (no FR_CHECK_FINITE).
+ * flags: FR_EDGE_ROUTE; with FR_ROUTING_D8 also FR_D8_LOWEST and FR_D4; with
+ * FR_ROUTING_MFD also FR_DINF (no FR_CHECK_FINITE).
  *   tiles_host  [ntiles] host array (read during the call only).
  *   tiles_dev   [ntiles] device copy of the same array, provided by the
  *               caller (so that no host memory is read at execution time).
@@ -324,10 +326,11 @@ size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_
 
 /*
  * Autotuner of the batched route: runs fr_route_batch with several CTA counts
- * for its persistent stages (synchronising the stream after each trial) and
- * keeps the fastest for later fr_route_batch calls of the same kind in this
- * process.  Same arguments as fr_route_batch; not for use during stream
- * capture.  The outputs hold a valid result afterwards.
+ * for its persistent receiver stage and, for D8, each inner-tile geometry of
+ * the local stage (128x32, 64x32, 96x48), synchronising the stream after each
+ * trial, and keeps the fastest for later fr_route_batch calls of the same
+ * kind in this process.  Same arguments as fr_route_batch; not for use during
+ * stream capture.  The outputs hold a valid result afterwards.
  */
 fr_status fr_batch_autotune(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
                             int32_t kind, double p, uint32_t flags, void* ws, size_t ws_bytes,
