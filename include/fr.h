@@ -55,7 +55,7 @@ typedef enum {
     FR_ERR_WORKSPACE = 3,   /* workspace NULL, too small or not 256-byte aligned */
     FR_ERR_NONFINITE = 4,   /* FR_CHECK_FINITE: the DEM holds NaN or Inf */
     FR_ERR_NO_PROGRESS = 5, /* device: not every cell was reached (cycle in the routing) */
-    FR_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    FR_ERR_UNSUPPORTED = 6  /* valid request the library does not implement (dL/dz under FR_DINF) */
 } fr_status;
 
 /* ---- flags ---------------------------------------------------------------
