@@ -150,6 +150,18 @@ def job_value(world, steps, cells, total_ms):
 
 
 # ----------------------------------------------------------------- reference
+METRIC = "cells routed/sec at 1 GB300 (D8 & slope-split)"
+
+
+def step_config(n, world, cells):
+    """The `config` of the step's JSON line (the same for both arms)."""
+    return {"workload": "D8 %dx%d fractal DEM (beta=2, tilt=0.01, jitter 1e-4 m, dx=30 m), "
+                        "rain U[0,1): receivers + two-float rain accumulation + uint64 "
+                        "unit-rain areas + mass balance" % (n, n),
+            "global_batch": world, "cells_per_step": cells,
+            "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -170,14 +182,15 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = args.steps * side * side / dt
     line = {
-        "impl": "reference", "metric": "cells routed/sec (D8)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "D8 fractal DEM beta=2 tilt=0.01 dx=30, rain U[0,1)",
-                   "sample": "%dx%d per step (full workload %dx%d)" % (side, side, N_SIDE, N_SIDE)},
+        "config": step_config(N_SIDE, args.gpus, N_SIDE * N_SIDE),
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": "%dx%d DEM per step, sequential high-to-low" % (side, side)},
+                         "sample": "%dx%d crop of the workload's recipe per step (receivers, "
+                                   "water, areas, mass balance; sequential high-to-low, "
+                                   "FP64/uint64), scaled to cells/s" % (side, side)},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -304,15 +317,11 @@ def main():
         cpu = cpu_baseline(z_np, r_np)
 
     line = {
-        "metric": "cells routed/sec at 1 GB300 (D8 & slope-split)",
+        "metric": METRIC,
         "value": value, "unit": "cells/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "D8 %dx%d fractal DEM (beta=2, tilt=0.01, jitter 1e-4 m, dx=30 m), "
-                               "rain U[0,1): receivers + two-float rain accumulation + uint64 "
-                               "unit-rain areas + mass balance" % (n, n),
-                   "global_batch": world, "cells_per_step": cells,
-                   "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas"},
+        "config": step_config(n, world, cells),
         "phases_ms": {"receivers": statistics.mean(recv_ms), "accumulate": statistics.mean(acc_ms),
                       "mass_balance": statistics.mean(mb_ms)},
         "roofline": {"bound": "hbm", "kernel": "fr_accumulate D8 (k_local_d8 + k_global)",
