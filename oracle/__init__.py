@@ -101,6 +101,8 @@ def lib():
                                         ctypes.c_int, P, P]
         L.or_mfd_delta_loss.restype = ctypes.c_double
         L.or_sink_of.restype = I64
+        L.or_fill.argtypes = [P, I64, I64, P]
+        L.or_fill.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -301,3 +303,15 @@ def route_mfd(z, dx, p=1.1, rain=None, flags: int = 0):
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+def fill(z) -> np.ndarray:
+    """Depression filling (the step before the path, Sec. 4): the least surface
+    F >= z, equal to z on the edge, in which every interior cell has a
+    neighbour lower by at least one fp32 step (priority-flood)."""
+    z = _f32(z)
+    ny, nx = z.shape
+    out = np.empty_like(z)
+    if lib().or_fill(_p(z), nx, ny, _p(out)) != 0:
+        raise MemoryError("or_fill: out of memory")
+    return out

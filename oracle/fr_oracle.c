@@ -609,3 +609,82 @@ double or_mfd_delta_loss(const double* z, int64_t nx, int64_t ny, double dx, dou
     free(heap);
     return dL;
 }
+
+/* ------------------------------------------------------------------ depression filling
+ * The paper routes a depression-filled DEM (Sec. 4); filling is the step before
+ * the path.  Reading taken: the least surface F >= z that keeps every edge
+ * cell at its own elevation and gives every interior cell a neighbour (of 8)
+ * that is strictly lower, by at least one fp32 step -- so that D8 routing on F
+ * has sinks only on the edge.  Equivalently, the unique solution of
+ *     F_c = z_c at edge cells,
+ *     F_c = max(z_c, min over neighbours n of succ(F_n)) elsewhere,
+ * succ(x) being the next fp32 value above x.  Computed by priority-flood: the
+ * edge cells seed a min-heap; each popped cell gives every not yet reached
+ * neighbour n the value max(z_n, succ(F_c)).  Cells leave the heap in
+ * non-decreasing F, so each cell is reached from its lowest neighbour. */
+static float succf(float x) { return nextafterf(x, INFINITY); }
+
+typedef struct { float f; int64_t i; } fill_item;
+
+static int fill_before(fill_item a, fill_item b) { return a.f < b.f || (a.f == b.f && a.i < b.i); }
+
+static void fill_push(fill_item* h, int64_t* n, fill_item it) {
+    int64_t k = (*n)++;
+    h[k] = it;
+    while (k > 0) {
+        int64_t p = (k - 1) / 2;
+        if (!fill_before(h[k], h[p])) break;
+        fill_item t = h[k]; h[k] = h[p]; h[p] = t;
+        k = p;
+    }
+}
+
+static fill_item fill_pop(fill_item* h, int64_t* n) {
+    fill_item top = h[0];
+    h[0] = h[--(*n)];
+    int64_t k = 0;
+    for (;;) {
+        int64_t l = 2 * k + 1, r = l + 1, m = k;
+        if (l < *n && fill_before(h[l], h[m])) m = l;
+        if (r < *n && fill_before(h[r], h[m])) m = r;
+        if (m == k) break;
+        fill_item t = h[k]; h[k] = h[m]; h[m] = t;
+        k = m;
+    }
+    return top;
+}
+
+int or_fill(const float* z, int64_t nx, int64_t ny, float* out) {
+    const int64_t n = nx * ny;
+    fill_item* heap = (fill_item*)malloc((size_t)n * sizeof(fill_item));
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    if (!heap || !seen) { free(heap); free(seen); return -1; }
+    int64_t hn = 0;
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            int64_t i = y * nx + x;
+            if (!is_edge(x, y, nx, ny)) continue;
+            out[i] = z[i];
+            seen[i] = 1;
+            fill_item it = {z[i], i};
+            fill_push(heap, &hn, it);
+        }
+    while (hn > 0) {
+        fill_item c = fill_pop(heap, &hn);
+        int64_t cx = c.i % nx, cy = c.i / nx;
+        for (int k = 0; k < 8; ++k) {
+            int64_t xn = cx + OFFX[k], yn = cy + OFFY[k];
+            if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+            int64_t j = yn * nx + xn;
+            if (seen[j]) continue;
+            seen[j] = 1;
+            float s = succf(c.f);
+            out[j] = z[j] > s ? z[j] : s;
+            fill_item it = {out[j], j};
+            fill_push(heap, &hn, it);
+        }
+    }
+    free(heap);
+    free(seen);
+    return 0;
+}

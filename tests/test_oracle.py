@@ -511,3 +511,81 @@ def test_dinf_invariants_and_dense_solve(seed):
     w = oracle.accumulate_mfd(f, order, rain)
     ref = np.linalg.solve(_dense_A_mfd(f), rain.astype(np.float64).ravel())
     np.testing.assert_allclose(w.ravel(), ref, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ depression filling
+def _relax_fill(z):
+    """Planchon-Darboux relaxation written independently of the oracle: start
+    from +inf inside and lower every interior cell to max(z, min over
+    neighbours of the next fp32 value above the neighbour) until nothing moves."""
+    z = np.asarray(z, np.float32)
+    ny, nx = z.shape
+    edge = np.zeros((ny, nx), bool)
+    edge[0, :] = edge[-1, :] = edge[:, 0] = edge[:, -1] = True
+    F = np.where(edge, z, np.float32(np.inf)).astype(np.float32)
+    while True:
+        P = np.full((ny + 2, nx + 2), np.inf, np.float32)
+        P[1:-1, 1:-1] = F
+        m = np.full((ny, nx), np.inf, np.float32)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dy or dx:
+                    m = np.minimum(m, np.nextafter(P[1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx],
+                                                   np.float32(np.inf)))
+        G = np.where(edge, z, np.maximum(z, np.minimum(F, m))).astype(np.float32)
+        if np.array_equal(G, F):
+            return F
+        F = G
+
+
+def test_fill_plane_is_unchanged():
+    """A plane falling towards the west edge already drains: filling is the identity."""
+    yy, xx = np.mgrid[0:9, 0:12]
+    z = (0.5 * xx + 0.01 * yy).astype(np.float32)
+    np.testing.assert_array_equal(oracle.fill(z), z)
+
+
+def test_fill_pit_by_hand():
+    """A 4x4 basin whose outlet is the corner at 4: the cell next to the outlet
+    sits one fp32 step above it, the others one step above that."""
+    z = np.array([[5, 5, 5, 5], [5, 1, 2, 5], [5, 3, 0, 5], [5, 5, 5, 4]], np.float32)
+    s1 = np.nextafter(np.float32(4), np.float32(np.inf))
+    s2 = np.nextafter(s1, np.float32(np.inf))
+    want = np.array([[5, 5, 5, 5], [5, s2, s2, 5], [5, s2, s1, 5], [5, 5, 5, 4]], np.float32)
+    np.testing.assert_array_equal(oracle.fill(z), want)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (2, 5), (3, 3), (7, 11), (16, 13), (24, 24)])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fill_matches_relaxation(shape, seed):
+    """Priority-flood against the independent relaxation, bit for bit, on rough
+    random surfaces (many pits and flats)."""
+    rng = np.random.default_rng(seed)
+    z = rng.integers(0, 6, size=shape).astype(np.float32)  # integer heights: many flats
+    np.testing.assert_array_equal(oracle.fill(z), _relax_fill(z))
+    z = rng.random(shape, dtype=np.float32) * 10
+    np.testing.assert_array_equal(oracle.fill(z), _relax_fill(z))
+
+
+def test_fill_invariants_and_drainage():
+    """On a fractal DEM: F >= z, edges unchanged, the defining equation holds at
+    every interior cell (so F is the least such surface), and D8 routing on F
+    leaves sinks only on the edge."""
+    z = inputs.fractal_dem(64, 80, beta=2.0, tilt=0.0, seed=5)
+    F = oracle.fill(z)
+    assert (F >= z).all()
+    np.testing.assert_array_equal(F[0], z[0])
+    np.testing.assert_array_equal(F[-1], z[-1])
+    np.testing.assert_array_equal(F[:, 0], z[:, 0])
+    np.testing.assert_array_equal(F[:, -1], z[:, -1])
+    P = np.full((66, 82), np.inf, np.float32)
+    P[1:-1, 1:-1] = F
+    m = np.full((64, 80), np.inf, np.float32)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy or dx:
+                m = np.minimum(m, np.nextafter(P[1 + dy:65 + dy, 1 + dx:81 + dx], np.float32(np.inf)))
+    np.testing.assert_array_equal(F[1:-1, 1:-1], np.maximum(z, m)[1:-1, 1:-1])
+    d = oracle.receivers_d8(F, 30.0)
+    assert (d[1:-1, 1:-1] != oracle.SINK).all()
+    assert (oracle.receivers_d8(z, 30.0)[1:-1, 1:-1] == oracle.SINK).any()  # the DEM had pits
