@@ -109,9 +109,10 @@ typedef enum {
     FR_OP_ADJOINT = 2,
     FR_OP_MASS_BALANCE = 3,
     FR_OP_ROUTE = 4, /* receivers + accumulate in one call (fr_route_d8) */
-    FR_OP_MFD = 5    /* any operation on an MFD routing (fr_accumulate, fr_route_mfd,
+    FR_OP_MFD = 5,   /* any operation on an MFD routing (fr_accumulate, fr_route_mfd,
                         fr_route_adjoint): the common workspace plus the fractions of
                         every cell, 32 bytes per cell */
+    FR_OP_FILL = 6   /* fr_fill: 256 bytes */
 } fr_op;
 
 /*
@@ -207,6 +208,30 @@ fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_o
  *   iterations_out   host int32 or NULL: iterations until exact.
  * Synchronises the stream after every sweep.  Workspace as fr_accumulate.
  */
+/*
+ * Depression filling, the step before the path: the paper routes a
+ * depression-filled DEM (Sec. 4).  filled_out receives the least surface
+ * F >= dem that keeps every edge cell at its own elevation and gives every
+ * interior cell a neighbour (of 8) lower by at least one fp32 step:
+ *     F = dem on the edge,  F_c = max(dem_c, succ(min over neighbours of F_n)),
+ * succ(x) the next fp32 value above x.  D8 routing on F (fr_receivers_d8,
+ * default flags) then has sinks only on the edge.  The result is unique and
+ * bit-reproducible.
+ *   dem          [ny*nx] float32, finite (FR_CHECK_FINITE checks it).
+ *   flags        0 or FR_CHECK_FINITE.
+ *   filled_out   [ny*nx] float32, not overlapping dem.
+ *   max_sweeps   >= 1: relaxation sweeps over 64x32 tiles allowed; a sweep
+ *                that changes nothing ends the call.  FR_ERR_NO_PROGRESS if
+ *                the surface is still moving after max_sweeps (filled_out
+ *                then holds an upper bound of F).
+ *   sweeps_out   host int32 or NULL: sweeps run, the last one changing nothing.
+ * Workspace: fr_workspace_size(FR_OP_FILL, nx, ny, flags) (256 bytes).
+ * Synchronises the stream after every sweep.
+ */
+fr_status fr_fill(const float* dem, int64_t nx, int64_t ny, uint32_t flags, float* filled_out,
+                  int32_t max_sweeps, int32_t* sweeps_out, void* ws, size_t ws_bytes,
+                  void* stream);
+
 fr_status fr_accumulate_richardson(const fr_routing* routing, const float* rain, float* w_out,
                                    float* w_lo_out, int32_t order, int32_t max_iterations,
                                    int32_t* iterations_out, void* ws, size_t ws_bytes,

@@ -42,6 +42,7 @@ FR_OP_ADJOINT = 2
 FR_OP_MASS_BALANCE = 3
 FR_OP_ROUTE = 4
 FR_OP_MFD = 5
+FR_OP_FILL = 6
 
 # Largest grid (cells) fr_route_d8_noalloc accepts.
 FR_NOALLOC_MAX_CELLS = 1 << 20
@@ -50,7 +51,7 @@ FR_NOALLOC_MAX_CELLS = 1 << 20
 EXPORTS = (
     "fr_receivers_d8", "fr_receivers_mfd", "fr_accumulate", "fr_route_d8", "fr_route_mfd",
     "fr_route_adjoint", "fr_mass_balance", "fr_route_batch", "fr_batch_workspace_size",
-    "fr_batch_autotune", "fr_route_d8_noalloc", "fr_accumulate_richardson",
+    "fr_batch_autotune", "fr_route_d8_noalloc", "fr_accumulate_richardson", "fr_fill",
     "fr_workspace_size", "fr_get_status", "fr_status_string", "fr_version",
 )
 
@@ -103,6 +104,8 @@ def load(build_if_missing: bool = True):
             "fr_receivers_d8": (S, [P, I64, I64, D, U32, P, P, P]),
             "fr_receivers_mfd": (S, [P, I64, I64, D, D, U32, P, P, P, P]),
             "fr_accumulate": (S, [ctypes.POINTER(fr_routing), P, P, P, P, P, ctypes.c_size_t, P]),
+            "fr_fill": (S, [P, I64, I64, U32, P, I32, ctypes.POINTER(ctypes.c_int32), P,
+                            ctypes.c_size_t, P]),
             "fr_accumulate_richardson": (S, [ctypes.POINTER(fr_routing), P, P, P, I32, I32,
                                              ctypes.POINTER(ctypes.c_int32), P, ctypes.c_size_t, P]),
             "fr_route_d8": (S, [P, I64, I64, D, U32, P, P, P, P, P, P, ctypes.c_size_t, P]),

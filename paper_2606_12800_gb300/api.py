@@ -13,7 +13,8 @@ from typing import Dict, Optional
 import torch
 
 from . import _lib
-from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_MFD, FR_OP_ROUTE, check, fr_routing, load)
+from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_FILL, FR_OP_MFD, FR_OP_ROUTE, check,
+                   fr_routing, load)
 
 _ws_cache: Dict[int, torch.Tensor] = {}
 
@@ -208,6 +209,19 @@ def accumulate_richardson(R: fr_routing, rain: Optional[torch.Tensor] = None, or
     if lo is not None:
         out["w_lo"] = lo
     return out, int(it.value)
+
+
+def fill(dem: torch.Tensor, max_sweeps: int = 100000, flags: int = 0):
+    """Depression filling (fr_fill): (filled DEM, sweeps run)."""
+    _check_grid(dem, torch.float32, "dem")
+    ny, nx = dem.shape
+    out = torch.empty_like(dem)
+    ws = torch.empty(int(load().fr_workspace_size(FR_OP_FILL, nx, ny, 0)), dtype=torch.uint8,
+                     device=dem.device)
+    sweeps = ctypes.c_int32(0)
+    check(load().fr_fill(_p(dem), nx, ny, flags, _p(out), int(max_sweeps), ctypes.byref(sweeps),
+                         _p(ws), ws.numel(), _stream()), "fr_fill")
+    return out, int(sweeps.value)
 
 
 def adjoint(R: fr_routing, w: torch.Tensor, w_lo: Optional[torch.Tensor] = None,

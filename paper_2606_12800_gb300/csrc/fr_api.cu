@@ -143,6 +143,7 @@ size_t fr_workspace_size(int32_t op, int64_t nx, int64_t ny, uint32_t flags) {
     if (!sizes_ok(nx, ny) || (flags & ~kKnownFlags)) return 0;
     if (op == FR_OP_RECEIVERS) return 0;
     if (op == FR_OP_MFD) return layout(nx * ny).total_mfd;
+    if (op == FR_OP_FILL) return 256;
     if (op < 0 || op > FR_OP_ROUTE) return 0;
     return layout(nx * ny).total;
 }
@@ -240,6 +241,35 @@ fr_status fr_accumulate(const fr_routing* R, const float* rain, float* w_out, fl
                         uint64_t* area_out, void* ws, size_t ws_bytes, void* stream) {
     return accumulate_impl(R, rain, w_out, w_lo_out, area_out, ws, ws_bytes, (cudaStream_t)stream,
                            false);
+}
+
+fr_status fr_fill(const float* dem, int64_t nx, int64_t ny, uint32_t flags, float* filled_out,
+                  int32_t max_sweeps, int32_t* sweeps_out, void* ws, size_t ws_bytes,
+                  void* stream) {
+    if (!dem || !filled_out || !sizes_ok(nx, ny) || max_sweeps < 1 || (flags & ~FR_CHECK_FINITE))
+        return FR_ERR_INVALID_ARG;
+    const int64_t n = nx * ny;
+    const uintptr_t a0 = (uintptr_t)dem, b0 = (uintptr_t)filled_out, len = (uintptr_t)n * 4;
+    if (a0 < b0 + len && b0 < a0 + len) return FR_ERR_INVALID_ARG;  // overlap
+    if (!ws || ws_bytes < 256 || ((uintptr_t)ws & 255)) return FR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & FR_CHECK_FINITE) {
+        fr_status st = check_finite(dem, n, s);
+        if (st != FR_OK) return st;
+    }
+    if (fill_init(dem, nx, ny, filled_out, s) != cudaSuccess) return FR_ERR_CUDA;
+    unsigned long long* changed = reinterpret_cast<unsigned long long*>(ws);
+    for (int32_t sweep = 1; sweep <= max_sweeps; ++sweep) {
+        unsigned long long h = 0;
+        if (cudaMemsetAsync(changed, 0, sizeof(h), s) != cudaSuccess) return FR_ERR_CUDA;
+        if (fill_sweep(dem, nx, ny, filled_out, changed, s) != cudaSuccess) return FR_ERR_CUDA;
+        if (cudaMemcpyAsync(&h, changed, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return FR_ERR_CUDA;
+        if (sweeps_out) *sweeps_out = sweep;
+        if (h == 0) return FR_OK;
+    }
+    return FR_ERR_NO_PROGRESS;
 }
 
 fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float* w_out,

@@ -47,6 +47,7 @@ def test_workspace_size(lib):
     # MFD operations keep 8 fp32 fractions per cell on top of the common part
     m = lib.fr_workspace_size(_lib.FR_OP_MFD, 4096, 4096, 0)
     assert m >= n + 4096 * 4096 * 32 and m % 256 == 0
+    assert lib.fr_workspace_size(_lib.FR_OP_FILL, 4096, 4096, 0) == 256
 
 
 def test_argument_validation_is_synchronous(lib):
@@ -63,6 +64,12 @@ def test_argument_validation_is_synchronous(lib):
     # D4 is a D8-only rule
     assert lib.fr_receivers_mfd(fake, 4, 4, 1.0, 1.1, _lib.FR_D4, fake, None, None, None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_workspace_size(_lib.FR_OP_ROUTE, 4, 4, _lib.FR_D4) > 0
+    # fill: overlapping input and output, no sweeps, unknown flags, small workspace
+    n = ctypes.c_int32(0)
+    assert lib.fr_fill(fake, 4, 4, 0, P(0x1010), 10, ctypes.byref(n), fake, 256, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_fill(fake, 4, 4, 0, P(0x100000), 0, None, fake, 256, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_fill(fake, 4, 4, _lib.FR_EDGE_ROUTE, P(0x100000), 5, None, fake, 256, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_fill(fake, 4, 4, 0, P(0x100000), 5, None, fake, 16, None) == _lib.FR_ERR_WORKSPACE
     # D-infinity is an MFD-only split
     assert lib.fr_receivers_d8(fake, 4, 4, 1.0, _lib.FR_DINF, fake, None, None) == _lib.FR_ERR_INVALID_ARG
     # fractions need 16-byte alignment

@@ -541,3 +541,39 @@ def test_autograd_route_mfd(api):
     assert relerr(rt.grad.cpu().numpy(), g_ref) <= RTOL_W
     dz = zt.grad.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(dz - dz_ref)) <= 1e-4 * np.abs(dz_ref).max()
+
+
+# ------------------------------------------------------------------ depression filling
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (2, 7), (3, 3), (33, 65), (64, 32), (97, 131),
+                                   (300, 517)])
+def test_fill_parity(api, shape):
+    """fr_fill against the priority-flood oracle, bit for bit: a fractal
+    surface and an integer-valued one (wide flats and many equal neighbours)."""
+    rng = np.random.default_rng(shape[0] * 1000 + shape[1])
+    for z in (inputs.fractal_dem(*shape, beta=2.0, tilt=0.0, seed=11),
+              rng.integers(0, 6, size=shape).astype(np.float32)):
+        F, sweeps = api.fill(cuda(z))
+        np.testing.assert_array_equal(F.cpu().numpy(), oracle.fill(z))
+        assert sweeps >= 1
+
+
+def test_fill_large_basins_drain_to_edge(api):
+    """A 1024x1536 surface with wide closed basins (beta 2.2, no tilt): the fill
+    matches the oracle bit for bit, D8 routing on it has sinks only on the
+    edge, and a call allowed one sweep reports FR_ERR_NO_PROGRESS."""
+    z = inputs.fractal_dem(1024, 1536, beta=2.2, tilt=0.0, seed=12)
+    F, sweeps = api.fill(cuda(z))
+    np.testing.assert_array_equal(F.cpu().numpy(), oracle.fill(z))
+    d = api.receivers_d8(F, 30.0).cpu().numpy()
+    assert (d[1:-1, 1:-1] != oracle.SINK).all()
+    assert sweeps > 1
+    with pytest.raises(Exception):
+        api.fill(cuda(z), max_sweeps=1)
+
+
+def test_fill_full_size_workload(api):
+    """The 4096^2 D8 benchmark DEM, filled, against the full oracle."""
+    n = 4096
+    z = inputs.fractal_dem(n, n, beta=2.0, tilt=0.01, seed=1)
+    F, _ = api.fill(cuda(z))
+    np.testing.assert_array_equal(F.cpu().numpy(), oracle.fill(z))
