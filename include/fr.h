@@ -112,7 +112,7 @@ typedef enum {
     FR_OP_MFD = 5,   /* any operation on an MFD routing (fr_accumulate, fr_route_mfd,
                         fr_route_adjoint): the common workspace plus the fractions of
                         every cell, 32 bytes per cell */
-    FR_OP_FILL = 6   /* fr_fill: 256 bytes */
+    FR_OP_FILL = 6   /* fr_fill: 256 bytes plus two bytes per 64x32 tile */
 } fr_op;
 
 /*
@@ -225,8 +225,8 @@ fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_o
  *                the surface is still moving after max_sweeps (filled_out
  *                then holds an upper bound of F).
  *   sweeps_out   host int32 or NULL: sweeps run, the last one changing nothing.
- * Workspace: fr_workspace_size(FR_OP_FILL, nx, ny, flags) (256 bytes).
- * Synchronises the stream after every sweep.
+ * Workspace: fr_workspace_size(FR_OP_FILL, nx, ny, flags).
+ * Synchronises the stream after every batch of eight sweeps.
  */
 fr_status fr_fill(const float* dem, int64_t nx, int64_t ny, uint32_t flags, float* filled_out,
                   int32_t max_sweeps, int32_t* sweeps_out, void* ws, size_t ws_bytes,

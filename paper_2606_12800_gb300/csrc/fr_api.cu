@@ -53,6 +53,13 @@ Layout layout(int64_t n) {
     return L;
 }
 
+// fr_fill's workspace: the sweep counters (one per sweep of a batch) and two
+// per-tile change records.
+constexpr int kFillBatch = 8;  // sweeps launched between two reads of the counters
+size_t fill_ws_bytes(int64_t nx, int64_t ny) {
+    return 256 + align256((size_t)fill_tiles(nx, ny)) * 2;
+}
+
 bool sizes_ok(int64_t nx, int64_t ny) {
     return nx >= 1 && ny >= 1 && nx < kMaxCells && ny < kMaxCells && nx <= kMaxCells / ny;
 }
@@ -143,7 +150,7 @@ size_t fr_workspace_size(int32_t op, int64_t nx, int64_t ny, uint32_t flags) {
     if (!sizes_ok(nx, ny) || (flags & ~kKnownFlags)) return 0;
     if (op == FR_OP_RECEIVERS) return 0;
     if (op == FR_OP_MFD) return layout(nx * ny).total_mfd;
-    if (op == FR_OP_FILL) return 256;
+    if (op == FR_OP_FILL) return fill_ws_bytes(nx, ny);
     if (op < 0 || op > FR_OP_ROUTE) return 0;
     return layout(nx * ny).total;
 }
@@ -251,23 +258,38 @@ fr_status fr_fill(const float* dem, int64_t nx, int64_t ny, uint32_t flags, floa
     const int64_t n = nx * ny;
     const uintptr_t a0 = (uintptr_t)dem, b0 = (uintptr_t)filled_out, len = (uintptr_t)n * 4;
     if (a0 < b0 + len && b0 < a0 + len) return FR_ERR_INVALID_ARG;  // overlap
-    if (!ws || ws_bytes < 256 || ((uintptr_t)ws & 255)) return FR_ERR_WORKSPACE;
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < fill_ws_bytes(nx, ny)) return FR_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags & FR_CHECK_FINITE) {
         fr_status st = check_finite(dem, n, s);
         if (st != FR_OK) return st;
     }
     if (fill_init(dem, nx, ny, filled_out, s) != cudaSuccess) return FR_ERR_CUDA;
-    unsigned long long* changed = reinterpret_cast<unsigned long long*>(ws);
-    for (int32_t sweep = 1; sweep <= max_sweeps; ++sweep) {
-        unsigned long long h = 0;
-        if (cudaMemsetAsync(changed, 0, sizeof(h), s) != cudaSuccess) return FR_ERR_CUDA;
-        if (fill_sweep(dem, nx, ny, filled_out, changed, s) != cudaSuccess) return FR_ERR_CUDA;
-        if (cudaMemcpyAsync(&h, changed, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    // counters of one batch of sweeps in the first 256 bytes, then the two
+    // per-tile change records (written by every sweep before they are read)
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);
+    uint8_t* act[2] = {(uint8_t*)ws + 256, (uint8_t*)ws + 256 + align256((size_t)fill_tiles(nx, ny))};
+    for (int32_t done = 0; done < max_sweeps;) {
+        const int32_t b = max_sweeps - done < kFillBatch ? max_sweeps - done : kFillBatch;
+        unsigned long long h[kFillBatch];
+        if (cudaMemsetAsync(counts, 0, sizeof(h), s) != cudaSuccess) return FR_ERR_CUDA;
+        for (int32_t k = 0; k < b; ++k) {
+            const int32_t sweep = done + k;  // 0-based
+            if (fill_sweep(dem, nx, ny, filled_out, act[(sweep + 1) & 1], act[sweep & 1],
+                           sweep == 0, counts + k, s) != cudaSuccess)
+                return FR_ERR_CUDA;
+        }
+        if (cudaMemcpyAsync(h, counts, sizeof(h[0]) * b, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return FR_ERR_CUDA;
-        if (sweeps_out) *sweeps_out = sweep;
-        if (h == 0) return FR_OK;
+        for (int32_t k = 0; k < b; ++k) {
+            if (h[k] == 0) {  // the first sweep that changed nothing; later ones were idle
+                if (sweeps_out) *sweeps_out = done + k + 1;
+                return FR_OK;
+            }
+        }
+        done += b;
+        if (sweeps_out) *sweeps_out = done;
     }
     return FR_ERR_NO_PROGRESS;
 }

@@ -17,6 +17,10 @@
 // newer within the sweep; both are upper bounds, so the result is the same.
 // The host repeats sweeps until one changes nothing: then every cell meets
 // its equation, and the surface is the unique solution, bit for bit.
+//
+// A tile whose 3x3 neighbourhood of tiles changed nothing in the previous
+// sweep is skipped (its cells and its ring are as they were when it last
+// settled); each CTA records whether its tile changed, for the next sweep.
 #include "fr_internal.h"
 
 namespace fr {
@@ -49,13 +53,30 @@ __global__ void __launch_bounds__(kFNT) k_fill_init(const float* __restrict__ z,
 
 __global__ void __launch_bounds__(kFNT) k_fill_sweep(const float* __restrict__ z, int64_t nx,
                                                      int64_t ny, float* F,
+                                                     const uint8_t* __restrict__ act_prev,
+                                                     uint8_t* __restrict__ act_next, int first,
                                                      unsigned long long* changed) {
     __shared__ float fs[kFRY * kFRX];
     __shared__ float zs[kFTY * kFTX];
     const float inf = __int_as_float(0x7f800000);
     const int tiles_x = (int)((nx + kFTX - 1) / kFTX);
+    const int tiles_y = (int)((ny + kFTY - 1) / kFTY);
     const int ty = (int)blockIdx.x / tiles_x, tx = (int)blockIdx.x - ty * tiles_x;
     const int64_t x0 = (int64_t)tx * kFTX, y0 = (int64_t)ty * kFTY;
+    if (!first) {
+        // run only if this tile or one of its 8 neighbour tiles changed last sweep
+        bool active = false;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int ux = tx + dx, uy = ty + dy;
+                if (ux >= 0 && uy >= 0 && ux < tiles_x && uy < tiles_y && act_prev[uy * tiles_x + ux])
+                    active = true;
+            }
+        if (!active) {
+            if (threadIdx.x == 0) act_next[blockIdx.x] = 0;
+            return;
+        }
+    }
     for (int i = threadIdx.x; i < kFRY * kFRX; i += kFNT) {
         const int ry = i / kFRX, rx = i - ry * kFRX;
         const int64_t gx = x0 + rx - 1, gy = y0 + ry - 1;
@@ -95,6 +116,7 @@ __global__ void __launch_bounds__(kFNT) k_fill_sweep(const float* __restrict__ z
         if (!__syncthreads_or(moved)) break;
         any = true;
     }
+    if (threadIdx.x == 0) act_next[blockIdx.x] = any ? 1 : 0;
     if (!any) return;
     for (int i = threadIdx.x; i < kFTY * kFTX; i += kFNT) {
         const int ly = i / kFTX, lx = i - ly * kFTX;
@@ -113,10 +135,14 @@ cudaError_t fill_init(const float* z, int64_t nx, int64_t ny, float* F, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t fill_sweep(const float* z, int64_t nx, int64_t ny, float* F,
-                       unsigned long long* changed, cudaStream_t s) {
-    const int64_t tiles = ((nx + kFTX - 1) / kFTX) * ((ny + kFTY - 1) / kFTY);
-    k_fill_sweep<<<(unsigned)tiles, kFNT, 0, s>>>(z, nx, ny, F, changed);
+int64_t fill_tiles(int64_t nx, int64_t ny) {
+    return ((nx + kFTX - 1) / kFTX) * ((ny + kFTY - 1) / kFTY);
+}
+
+cudaError_t fill_sweep(const float* z, int64_t nx, int64_t ny, float* F, const uint8_t* act_prev,
+                       uint8_t* act_next, bool first, unsigned long long* changed, cudaStream_t s) {
+    k_fill_sweep<<<(unsigned)fill_tiles(nx, ny), kFNT, 0, s>>>(z, nx, ny, F, act_prev, act_next,
+                                                              first ? 1 : 0, changed);
     return cudaGetLastError();
 }
 

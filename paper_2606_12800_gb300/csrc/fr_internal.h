@@ -95,10 +95,13 @@ cudaError_t richardson_sweep(bool mfd, const Prob& P, const float2* prev, float2
                              unsigned long long* counts, cudaStream_t s);
 cudaError_t richardson_output(const float2* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 // Depression filling (fr_fill.cu): F = z on the edge and +inf inside, then one
-// relaxation sweep over 64x32 tiles; *changed counts the tiles that moved.
+// relaxation sweep over 64x32 tiles; *changed counts the tiles that moved and
+// act_next[t] records it per tile (act_prev: the previous sweep's record,
+// unused when first).
+int64_t fill_tiles(int64_t nx, int64_t ny);
 cudaError_t fill_init(const float* z, int64_t nx, int64_t ny, float* F, cudaStream_t s);
-cudaError_t fill_sweep(const float* z, int64_t nx, int64_t ny, float* F,
-                       unsigned long long* changed, cudaStream_t s);
+cudaError_t fill_sweep(const float* z, int64_t nx, int64_t ny, float* F, const uint8_t* act_prev,
+                       uint8_t* act_next, bool first, unsigned long long* changed, cudaStream_t s);
 cudaError_t launch_mfd_fractions(const float* z, const uint8_t* mask, int64_t nx, int64_t ny,
                                  double dx, double p, uint32_t flags, float* frac, cudaStream_t s);
 cudaError_t launch_receivers_batch(int kind, const Prob* probs, const int64_t* prefix, int nprob,

@@ -47,7 +47,9 @@ def test_workspace_size(lib):
     # MFD operations keep 8 fp32 fractions per cell on top of the common part
     m = lib.fr_workspace_size(_lib.FR_OP_MFD, 4096, 4096, 0)
     assert m >= n + 4096 * 4096 * 32 and m % 256 == 0
-    assert lib.fr_workspace_size(_lib.FR_OP_FILL, 4096, 4096, 0) == 256
+    # fill: a batch of sweep counters plus two change records per 64x32 tile
+    f = lib.fr_workspace_size(_lib.FR_OP_FILL, 4096, 4096, 0)
+    assert f >= 256 + 2 * (4096 // 64) * (4096 // 32) and f % 256 == 0
 
 
 def test_argument_validation_is_synchronous(lib):
