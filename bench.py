@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the MFD/batch/adjoint rows")
-    ap.add_argument("--rows", default="slope_split,batched,adjoint,d8_32768,richardson",
+    ap.add_argument("--rows", default="slope_split,batched,adjoint,d8_32768,richardson,fill",
                     help="comma-separated extra rows to run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -415,6 +415,8 @@ def extra_rows(api, L, dev, peak, want):
         torch.cuda.empty_cache()
     if "richardson" in want:
         rows["richardson"] = richardson_row(api, dev, timed)
+    if "fill" in want:
+        rows["fill"] = fill_row(api, peak, timed)
         torch.cuda.empty_cache()
     return rows
 
@@ -477,6 +479,29 @@ def d8_large_row(api, L, dev, peak, timed):
             "accumulate_roofline": {"bound": "hbm", "algorithmic_bytes_per_cell": 9,
                                     "achieved_gbs": cells * 9 / (ms_acc * 1e-3) / 1e9, "peak": peak,
                                     "frac": cells * 9 / (ms_acc * 1e-3) / 1e9 / peak}}
+
+
+def fill_row(api, peak, timed):
+    """Depression filling (fr_fill) of the D8 step's DEM (4096^2, beta 2, tilt
+    0.01) and of the slope-split DEM (8192^2, beta 2.2, no tilt: wide closed
+    basins): sweeps to the exact fill and device time, against the roofline at
+    8 algorithmic bytes per cell (z in, F out)."""
+    from paper_2606_12800_gb300 import inputs
+    out = {}
+    for name, n, beta, tilt, seed in (("d8_4096", N_SIDE, 2.0, 0.01, SEED),
+                                      ("mfd_8192", MFD_SIDE, 2.2, 0.0, SEED + 2)):
+        z = inputs.fractal_dem_torch(n, n, beta=beta, tilt=tilt, seed=seed, device="cuda")
+        res = {}
+
+        def run():
+            res["F"], res["sweeps"] = api.fill(z)
+        ms = timed(run, reps=3)
+        gbs = n * n * 8 / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "sweeps": res["sweeps"], "cells_per_s": n * n / (ms * 1e-3),
+                     "raised_frac": float((res["F"] != z).float().mean().item()),
+                     "hbm_frac": gbs / peak}
+        del z, res
+    return out
 
 
 def richardson_row(api, dev, timed):

@@ -7,6 +7,7 @@ Cases (all on seeded synthetic fractal DEMs, inputs resident on the device):
   mfd       slope-split route (p = 1.1), unit rain
   adjoint   slope-split route, then the adjoint of L = sum over sinks of w^2
             (dL/drain and dL/dz)
+  fill      depression filling of the D8 DEM (beta 2, tilt 0.01)
 Each case runs ``--reps`` times and prints the device status word.
 """
 import argparse
@@ -18,13 +19,17 @@ from . import api, inputs
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=["d8", "d8_area", "mfd", "adjoint"])
+    ap.add_argument("case", choices=["d8", "d8_area", "mfd", "adjoint", "fill"])
     ap.add_argument("--n", type=int, default=4096, help="grid side (n x n)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1)
     a = ap.parse_args(argv)
     n, dev = a.n, torch.device("cuda", torch.cuda.current_device())
-    if a.case.startswith("d8"):
+    if a.case == "fill":
+        z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.01, seed=a.seed, device="cuda")
+        for _ in range(a.reps):
+            api.fill(z)
+    elif a.case.startswith("d8"):
         z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.01, seed=a.seed, device="cuda")
         rain = None if a.case == "d8_area" else inputs.rain_field_torch(n, n, a.seed, device="cuda")
         d = api.receivers_d8(z, 30.0)

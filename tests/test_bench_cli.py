@@ -11,7 +11,7 @@ sys.path.insert(0, str(ROOT))
 
 def test_default_rows_have_functions():
     import bench
-    for name in ("extra_rows", "batch_rows", "adjoint_row", "d8_large_row", "richardson_row",
+    for name in ("extra_rows", "batch_rows", "adjoint_row", "d8_large_row", "richardson_row", "fill_row",
                  "cpu_baseline", "run_reference"):
         assert callable(getattr(bench, name)), name
 
