@@ -72,9 +72,9 @@ struct SmemD8 {
     alignas(16) uint32_t pk[NR];                  // packed arrivals / donors' area
     alignas(16) uint8_t code[NR];                 // receiver codes of region + ring, padded rows
     alignas(16) uint8_t dm[W ? NR : 16];          // donor masks (value pulls)
-    uint16_t queue[Gm::NE];                       // walker starts (ring indices)
-    int qtail;                                    // number of starts
-    int head;                                     // next start to hand out
+    uint16_t queue[Gm::NE];                       // ready list: cells whose donors (all leaves) finished in the leaf pass
+    int qtail;                                    // its length
+    int head;                                     // next entry to hand out
     unsigned long long done;
 };
 
@@ -99,9 +99,10 @@ __device__ __forceinline__ void push4(S_& S, const int (&cq)[4]) {
         if (cq[q] >= 0) S.queue[pos++] = (uint16_t)cq[q];
 }
 
-// Warp-aggregated append of up to four starts per lane (all lanes call).
+// Warp-aggregated append of up to four cells per lane to the ready list (all
+// lanes call; the scalar path).
 template <class S_>
-__device__ __forceinline__ void push_starts(S_& S, int n, const int (&cells)[4]) {
+__device__ __forceinline__ void push_cells(S_& S, int n, const int (&cells)[4]) {
     const unsigned lane = threadIdx.x & 31u;
     int incl = n;
 #pragma unroll
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
                 }
                 // outside the grid: no preset, no donors; never final
             }
-            push_starts(S, n, cells);
+            push_cells(S, n, cells);
         }
     }
     __syncthreads();
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
         const int nst = S.qtail;
         int c = -1;        // ring index of the cell being finalised
         uint32_t a = 0;    // its local area
-        bool more = true;  // warp-uniform: starts may be left
+        bool more = true;  // warp-uniform: list entries may be left
         for (;;) {
             if (more) {
                 const unsigned idle = __ballot_sync(0xffffffffu, c < 0);
