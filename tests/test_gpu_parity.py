@@ -404,10 +404,11 @@ def _donor_lists(recv_of, n):
     return deps
 
 
-@pytest.mark.parametrize("shape", [(33, 65), (97, 131), (256, 300)])
+@pytest.mark.parametrize("shape", [(32, 64), (20, 45), (33, 65), (97, 131), (256, 300)])
 def test_richardson_d8_exact_after_c_plus_one(api, shape):
     """Richardson I+X on 64x32 tiles: the result of the exact solve, after
-    exactly C + 1 iterations (C = most tile crossings of any stream)."""
+    exactly C + 1 iterations (C = most tile crossings of any stream).  A grid
+    of one tile (one "process": D^-1 = A^-1) is exact after one iteration."""
     ny, nx = shape
     z = inputs.fractal_dem(ny, nx, beta=2.0, tilt=0.01, seed=nx)
     d = api.receivers_d8(cuda(z), 30.0)
