@@ -86,6 +86,18 @@ typedef enum {
  *                  dL/dz of the adjoint is not available for it.
  *   FR_CHECK_FINITE reject a DEM holding NaN or Inf (FR_ERR_NONFINITE; this
  *                  check synchronises the stream).
+ * Global phase of D8 accumulation (fr_accumulate with a D8 routing, whose
+ * fr_routing.flags carry these, and fr_route_d8).  Cells whose upstream basin
+ * leaves their tile are finished either by walkers that follow the receivers
+ * one cell per step, or by a solve on the skeleton of a 64x64 tiling whose
+ * steps cross a whole tile (Sec. 2.4's skeleton of the domain decomposition);
+ * the second wins on DEMs with long rivers (depression-filled, planar), the
+ * first on rough ones.  By default the library picks the skeleton solve when
+ * at least 1/512 of the cells need the global phase.  Both give the same
+ * areas; real-valued water differs only in the order of two-float additions.
+ *   FR_GLOBAL_WALKERS  always the cell walkers.
+ *   FR_GLOBAL_SKELETON always the skeleton solve (grids too small for its
+ *                  scratch, under about 64x64 cells, use the walkers).
  */
 #define FR_EDGE_SINK 0x0u
 #define FR_EDGE_ROUTE 0x1u
@@ -94,6 +106,8 @@ typedef enum {
 #define FR_CHECK_FINITE 0x4u
 #define FR_D4 0x8u
 #define FR_DINF 0x10u
+#define FR_GLOBAL_WALKERS 0x20u
+#define FR_GLOBAL_SKELETON 0x40u
 
 #define FR_SINK 0xFFu
 
@@ -160,7 +174,8 @@ typedef struct {
                              fr_receivers_mfd's frac_out) */
     double dx;            /* MFD: grid spacing */
     double p;             /* MFD: slope exponent */
-    uint32_t flags;       /* MFD: the flags given to fr_receivers_mfd */
+    uint32_t flags;       /* MFD: the flags given to fr_receivers_mfd; D8: 0 or one of
+                             FR_GLOBAL_WALKERS / FR_GLOBAL_SKELETON */
     uint32_t reserved2;   /* must be 0 */
 } fr_routing;
 
@@ -188,27 +203,6 @@ fr_status fr_accumulate(const fr_routing* routing, const float* rain, float* w_o
                         void* stream);
 
 /*
- * The paper's own parallel solver, run on one GPU (Sec. 2.4, 3.3, 3.4,
- * App. B.1): Richardson iteration for the "I+X" form of A w = r,
- *     w^(l+1) = T(w^(l)),  T(w) = D^{-1} (r + R w),  w^(0) = 0
- * (Eq. richardson-I+X), with 64x32 tiles as the subdomains: D^{-1} is each
- * tile's exact high-to-low solve and R w passes water across tile
- * boundaries.  order = 1 is I+X.  order = 2 is the (I-X)(I+X) scheme of
- * Sec. 3.4: one Richardson step on the preconditioned system equals two
- * applications of T; order = k applies T k times per iteration (the longer
- * preconditioner series Sec. 3.4 mentions).  A stream crossing tile
- * boundaries C times is exact after C + 1 applications of T, that is after
- * ceil((C + 1) / order) iterations.  The loop stops at the first sweep that
- * changes no value; the result equals fr_accumulate's up to the order of
- * additions (also fixed here).  Offered as the paper's method for
- * comparison: fr_accumulate reaches the exact result in two launches.
- *   w_out, w_lo_out  as fr_accumulate (w_out required).
- *   order            1 .. 64.
- *   max_iterations   >= 1; FR_ERR_NO_PROGRESS if more would be needed.
- *   iterations_out   host int32 or NULL: iterations until exact.
- * Synchronises the stream after every sweep.  Workspace as fr_accumulate.
- */
-/*
  * Depression filling, the step before the path: the paper routes a
  * depression-filled DEM (Sec. 4).  filled_out receives the least surface
  * F >= dem that keeps every edge cell at its own elevation and gives every
@@ -232,13 +226,33 @@ fr_status fr_fill(const float* dem, int64_t nx, int64_t ny, uint32_t flags, floa
                   int32_t max_sweeps, int32_t* sweeps_out, void* ws, size_t ws_bytes,
                   void* stream);
 
+/*
+ * The paper's own parallel solver, run on one GPU (Sec. 2.4, 3.3, 3.4,
+ * App. B.1): Richardson iteration for the "I+X" form of A w = r,
+ *     w^(l+1) = T(w^(l)),  T(w) = D^{-1} (r + R w),  w^(0) = 0
+ * (Eq. richardson-I+X), with 64x32 tiles as the subdomains: D^{-1} is each
+ * tile's exact high-to-low solve and R w passes water across tile
+ * boundaries.  order = 1 is I+X.  order = 2 is the (I-X)(I+X) scheme of
+ * Sec. 3.4: one Richardson step on the preconditioned system equals two
+ * applications of T; order = k applies T k times per iteration (the longer
+ * preconditioner series Sec. 3.4 mentions).  A stream crossing tile
+ * boundaries C times is exact after C + 1 applications of T, that is after
+ * ceil((C + 1) / order) iterations.  The loop stops at the first sweep that
+ * changes no value; the result equals fr_accumulate's up to the order of
+ * additions (also fixed here).  Offered as the paper's method for
+ * comparison: fr_accumulate reaches the exact result in two launches.
+ *   w_out, w_lo_out  as fr_accumulate (w_out required).
+ *   order            1 .. 64.
+ *   max_iterations   >= 1; FR_ERR_NO_PROGRESS if more would be needed.
+ *   iterations_out   host int32 or NULL: iterations until exact.
+ * Synchronises the stream after every sweep.  Workspace as fr_accumulate.
+ */
 fr_status fr_accumulate_richardson(const fr_routing* routing, const float* rain, float* w_out,
                                    float* w_lo_out, int32_t order, int32_t max_iterations,
                                    int32_t* iterations_out, void* ws, size_t ws_bytes,
                                    void* stream);
 
 /*
- * Receivers + accumulation in one call (D8)/*
  * Receivers + accumulation in one call (D8): the direction grid goes to
  * dir_out if non-NULL, else to the workspace.  Outputs as fr_accumulate.
  * Workspace: fr_workspace_size(FR_OP_ROUTE, nx, ny, flags).

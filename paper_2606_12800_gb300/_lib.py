@@ -30,6 +30,8 @@ FR_D8_STEEPEST = 0x0
 FR_D8_LOWEST = 0x2
 FR_D4 = 0x8
 FR_DINF = 0x10
+FR_GLOBAL_WALKERS = 0x20
+FR_GLOBAL_SKELETON = 0x40
 FR_CHECK_FINITE = 0x4
 FR_SINK = 0xFF
 

@@ -53,11 +53,14 @@ def workspace(nx: int, ny: int, device=None, mfd: bool = False) -> torch.Tensor:
     return ws
 
 
-def routing_d8(dir_: torch.Tensor) -> fr_routing:
+def routing_d8(dir_: torch.Tensor, flags: int = 0) -> fr_routing:
+    """D8 routing descriptor; flags: 0, FR_GLOBAL_WALKERS or FR_GLOBAL_SKELETON
+    (the global phase of the accumulation, see fr.h)."""
     R = fr_routing()
     R.kind = FR_ROUTING_D8
     R.ny, R.nx = dir_.shape
     R.dir = dir_.data_ptr()
+    R.flags = flags
     R._keep = (dir_,)  # the descriptor holds raw pointers: keep the tensors alive
     return R
 

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restr
         P.glist = reinterpret_cast<unsigned long long*>(ws + L.glist);
         P.glist_cap = L.cells;
         P.mc = make_mfd_const(t.dx, kind == FR_ROUTING_MFD ? p : 1.0);
+        P.skel_min = ~0ull;  // batched D8: the cell walkers finish the global cells
         probs[i] = P;
         pre_recv[i] = o_rt;
         pre_eng[i] = o_et;

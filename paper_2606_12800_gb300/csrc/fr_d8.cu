@@ -520,7 +520,11 @@ cudaError_t launch_d8(const Prob& P, EngineGlobals* G, cudaStream_t s) {
     const int64_t tiles = ((P.nx + Gm::TX - 1) / Gm::TX) * ((P.ny + Gm::TY - 1) / Gm::TY);
     cudaError_t e = launch_local_d8<Gm, W, AREA, false>(P, G, nullptr, nullptr, 1, tiles, s);
     if (e != cudaSuccess) return e;
-    return launch_global<Mode::FwdD8, W, AREA>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
+    // both global phases are enqueued; each returns at once unless the
+    // global-cell count selects it (walkers below P.skel_min, skeleton above)
+    e = launch_global<Mode::FwdD8, W, AREA>(nullptr, P, G, (unsigned long long)(P.nx * P.ny), s);
+    if (e != cudaSuccess || P.skel_min == ~0ull) return e;
+    return launch_d8_skeleton(W, AREA, P, G, s);
 }
 
 template <class Gm, bool W, bool AREA>

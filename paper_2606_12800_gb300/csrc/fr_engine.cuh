@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(256) k_global_init(const Prob* __restrict__ pr
     using E = Eng<M, W, AREA>;
     const unsigned long long count = G->glist_count;
     const Prob& P0 = probs ? probs[0] : single;
+    if (count >= P0.skel_min) return;  // the skeleton solve takes the global cells
     const unsigned long long* list = P0.glist;
     unsigned long long* starts = reinterpret_cast<unsigned long long*>(P0.link);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -342,8 +343,9 @@ __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, 
     using E = Eng<M, W, AREA>;
     static_assert(E::kD8Fwd, "branching modes use k_global_levels");
     __shared__ unsigned long long s_done;
-    const unsigned long long count = G->fcount[0];
     const Prob& P0 = probs ? probs[0] : single;
+    if (__ldcg(&G->glist_count) >= P0.skel_min) return;  // the skeleton solve takes them
+    const unsigned long long count = G->fcount[0];
     const unsigned long long* starts = reinterpret_cast<const unsigned long long*>(P0.link);
     unsigned long long done = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;

@@ -40,6 +40,13 @@ struct Prob {
     int64_t glist_cap;     // capacity of glist (entries)
     MfdConst mc;
     int32_t lo_full;       // out_lo is a user output: write it for every cell
+    // D8 forward global phase: the tile-skeleton solve (fr_skel.cu) runs when
+    // the local phase leaves at least skel_min global cells, the cell walkers
+    // otherwise (~0: walkers always)
+    unsigned long long skel_min;
+    uint16_t* skpool;               // dependency slots, kSkelPool per skeleton tile
+    unsigned long long* skstarts;   // exits that start a skeleton walker
+    uint32_t* sktiles;              // skeleton tiles holding global cells
 };
 
 // Device-wide bookkeeping kept at the start of the workspace; zeroed (with
@@ -57,7 +64,8 @@ struct EngineGlobals {
     unsigned int bar_count;          // grid barrier: blocks arrived
     unsigned int bar_gen;            // grid barrier: generation
     unsigned long long rounds;       // level-synchronous global phase: rounds run (diagnostic)
-    unsigned long long pad[4];
+    unsigned long long skel_tiles;   // skeleton solve: tiles listed in Prob::sktiles
+    unsigned long long pad[3];
 };
 static_assert(sizeof(EngineGlobals) == 128, "globals block is 128 bytes (256 reserved)");
 
@@ -65,6 +73,19 @@ enum class Mode : int { FwdD8 = 0, FwdMfd = 1, AdjD8 = 2, AdjMfd = 3 };
 
 // Grid of the D8 forward walker kernel (fr_accumulate.cu).
 int walker_grid();
+// Skeleton tiles of the D8 global phase (fr_skel.cu): kSkelTile x kSkelTile
+// cells; kSkelPool dependency slots per tile (a dependency is a donor in the
+// one-cell ring around the tile, and each ring cell has one receiver).
+constexpr int kSkelTile = 64;
+constexpr int kSkelPool = 4 * kSkelTile + 4;
+__host__ __device__ inline int64_t skel_tiles(int64_t nx, int64_t ny) {
+    return ((nx + kSkelTile - 1) / kSkelTile) * ((ny + kSkelTile - 1) / kSkelTile);
+}
+// Skeleton solve of the global cells left by the D8 forward local phase;
+// every kernel returns at once unless the global-cell count reaches
+// prob.skel_min.
+cudaError_t launch_d8_skeleton(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
+                               cudaStream_t s);
 // D8 forward: halo-tile local phase (fr_d8.cu) + walker phase.
 cudaError_t launch_d8_forward(bool want_w, bool want_area, const Prob& prob, EngineGlobals* g,
                               cudaStream_t s);

@@ -1,0 +1,693 @@
+// fr_skel.cu -- global phase of D8 forward accumulation on the skeleton of a
+// tile decomposition, for DEMs with long rivers.
+//
+// After the halo-tile local phase (fr_d8.cu) every cell is either final or
+// "global": its upstream basin leaves its tile's extended region.  On a rough
+// DEM global cells are rare and short, and the cell walkers of fr_engine.cuh
+// finish them in microseconds.  On a depression-filled DEM (the paper routes
+// one, Sec. 4) or on a plane, rivers run across the whole grid: the global
+// cells are the river trunks, thousands of cells long, and a walker that
+// follows a trunk one cell per dependent step takes tens to hundreds of
+// milliseconds.  This file solves the same global cells exactly on the
+// skeleton of a second, non-overlapping decomposition into 64x64 tiles, the
+// solve on "the skeleton of the domain decomposition" that Sec. 2.4 mentions,
+// made exact for single-receiver routing:
+//
+//  A. per tile (k_skel_a), in shared memory: every global cell i gets its
+//     in-tile partial value L(i) = c(i) + sum of L over its global donors in
+//     the tile, where c(i) = rain(i) + the final values of its non-global
+//     donors; an entry (a global cell with global donors in other tiles)
+//     learns, by pointer doubling along the in-tile receivers, the exit it
+//     drains to (a global cell whose receiver lies in another tile; D8 paths
+//     are unique), or that its path ends inside the tile.  Each exit x gets
+//     the list of its dependencies: the exits y of neighbouring tiles that
+//     drain into an entry whose path reaches x, in a fixed order.
+//  B. walkers over the exits (k_skel_walk): the total water of an exit is
+//         O(x) = L(x) + sum over its dependencies y of O(y);
+//     an exit with no dependency starts a walker, which computes O(x), then
+//     arrives at the exit its receiver drains to; the arrival that completes
+//     an exit's count continues there ("last arriver continues").  One step
+//     crosses a whole tile.
+//  C. per tile again (k_skel_fix): each entry's inflow (the sum of O over its
+//     donors in other tiles) is passed down the in-tile receivers and added
+//     to L of every global cell below it; exits keep O from B.
+//
+// Sums run in fixed orders (donors in code order, dependency lists in
+// row-major entry order), so results are bit-reproducible; they differ from
+// the cell walkers' only in the order of the two-float additions.  Unit-rain
+// areas are exact integers either way.  A routing graph with a cycle leaves
+// cells unfinished; the last CTA of C compares the count of finished cells
+// with the number of cells.
+#include <cuda/atomic>
+
+#include "fr_engine.cuh"
+
+namespace fr {
+namespace {
+
+constexpr int SX = kSkelTile, SY = kSkelTile, SN = SX * SY;
+constexpr int SRX = SX + 2, SRY = SY + 2, SRN = SRX * SRY;  // with a one-cell ring
+constexpr int kSkNT = 256;
+static_assert(SN <= 4096, "local indices take 12 bits");
+static_assert(kSkelPool == 2 * (SX + SY) + 4, "dependency slots per tile: the ring cells");
+
+// Cell byte of the ring arrays: the receiver code (bits 0-3; 15 = none, also
+// for receivers outside the grid) and the global flag.
+constexpr uint8_t kNoCode = 15, kGlob = 0x80;
+
+// Per-cell word of the in-tile walkers: pending in-tile global donors
+// (bits 0-3) and flags.
+constexpr uint32_t kFin = 1u << 31, kPoison = 1u << 30, kUp = 1u << 29;
+// Pointer-doubling word: a local index (bits 0-11), final (bit 12: the path
+// ends here), exit (bit 13: ... by leaving the tile).
+constexpr uint16_t kPtrFinal = 1u << 12, kPtrExit = 1u << 13;
+
+// Link word of a boundary cell (per cell, 8 bytes, in the workspace):
+//   exit:   kind 2, pending dependencies (bits 0-15), list begin (16-31),
+//           list length (32-47);
+//   entry:  kind 1, the exit its in-tile path reaches (cell index, bits 0-39);
+//   else 0 (an entry whose path ends inside its tile).
+constexpr unsigned long long kLkExit = 2ull << 62, kLkEntry = 1ull << 62, kLkKind = 3ull << 62;
+constexpr unsigned long long kLkCell = (1ull << 40) - 1;
+// Pending count of an exit whose in-tile partial value was never computed (a
+// cycle upstream of it inside its tile): never reached by arrivals.
+constexpr unsigned long long kLkNever = 0xFFFFull;
+
+struct TileGeo {
+    int64_t x0, y0;  // origin
+    int ex, ey;      // extent (partial tiles at the grid's far edges)
+    int tiles_x;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const Prob& P, int64_t t) {
+    TileGeo g;
+    g.tiles_x = (int)((P.nx + SX - 1) / SX);
+    const int64_t ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+    g.x0 = tx * SX;
+    g.y0 = ty * SY;
+    g.ex = (int)(P.nx - g.x0 < SX ? P.nx - g.x0 : SX);
+    g.ey = (int)(P.ny - g.y0 < SY ? P.ny - g.y0 : SY);
+    return g;
+}
+
+// Boundary cells of a tile in row-major order: index b <-> (lx, ly).
+__device__ __forceinline__ int nboundary(int ex, int ey) {
+    const int mid = ey > 2 ? ey - 2 : 0, per = ex > 1 ? 2 : 1;
+    return ex + mid * per + (ey > 1 ? ex : 0);
+}
+__device__ __forceinline__ void bcell(int b, int ex, int ey, int& lx, int& ly) {
+    const int mid = ey > 2 ? ey - 2 : 0, per = ex > 1 ? 2 : 1;
+    if (b < ex) {
+        lx = b;
+        ly = 0;
+        return;
+    }
+    b -= ex;
+    if (b < mid * per) {
+        ly = 1 + b / per;
+        lx = (b % per) ? ex - 1 : 0;
+        return;
+    }
+    lx = b - mid * per;
+    ly = ey - 1;
+}
+__device__ __forceinline__ int bindex(int lx, int ly, int ex, int ey) {
+    const int mid = ey > 2 ? ey - 2 : 0, per = ex > 1 ? 2 : 1;
+    if (ly == 0) return lx;
+    if (ly == ey - 1) return ex + mid * per + lx;
+    return ex + (ly - 1) * per + (lx == 0 ? 0 : 1);
+}
+
+template <bool W, bool AREA>
+struct SmemSk {
+    uint8_t cg[SRN];                        // ring layout: code | kGlob
+    alignas(16) uint32_t pk[SN];            // walker words (inner cells)
+    uint16_t qp[SN];                        // walker start list, then pointer doubling
+    float hi[W ? SN : 1], lo[W ? SN : 1];   // two-float values (L in A, inflow sums in C)
+    unsigned long long ar[AREA ? SN : 1];   // areas
+    uint16_t bslots[SX * 4];                // per boundary cell: dependency slots (exits: list length)
+    uint16_t bbeg[SX * 4];                  // per exit: list begin
+    uint16_t brank[SX * 4];                 // per entry: offset in its exit's list
+    uint8_t wtmp[32];                       // warp-0 scratch
+    int qtail, head, tile_ok;
+    unsigned long long done;
+};
+
+__device__ __forceinline__ bool in_ext(int lx, int ly, const TileGeo& g) {
+    return lx >= 0 && ly >= 0 && lx < g.ex && ly < g.ey;
+}
+
+// Loads the receiver codes and global flags of a tile and its ring.  Returns
+// (block-uniform) whether the tile holds a global cell.
+template <class S_>
+__device__ bool load_ring(S_& S, const Prob& P, const TileGeo& g) {
+    int any = 0;
+    for (int i = threadIdx.x; i < SRN; i += kSkNT) {
+        const int ry = i / SRX, rx = i - ry * SRX;
+        const int64_t gx = g.x0 - 1 + rx, gy = g.y0 - 1 + ry;
+        uint8_t c = kNoCode;
+        if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
+            const int64_t gi = gy * P.nx + gx;
+            const uint8_t k = rd_rb(P, gi);
+            if (k < 8) {
+                const int64_t tx = gx + offx(k), ty = gy + offy(k);
+                if (tx >= 0 && ty >= 0 && tx < P.nx && ty < P.ny) c = k;
+            }
+            if (gbit(P, gi)) {
+                c |= kGlob;
+                if (rx >= 1 && ry >= 1 && rx <= g.ex && ry <= g.ey) any = 1;
+            }
+        }
+        S.cg[i] = c;
+    }
+    return __syncthreads_or(any) != 0;
+}
+
+// Warp-aggregated append of one optional local cell per lane (all lanes call).
+template <class S_>
+__device__ __forceinline__ void push_start(S_& S, int cell) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, cell >= 0);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(&S.qtail, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cell >= 0) S.qp[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)cell;
+}
+
+// In-tile walker solve over the global cells: a cell is finalised once its
+// in-tile global donors are (its value: its own start value plus theirs in
+// code order; flags or-ed), then arrives at its in-tile global receiver; the
+// arrival that completes the receiver's count continues there.
+template <bool W, bool AREA, class S_>
+__device__ void tile_walk(S_& S, const TileGeo& g) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    const int nst = S.qtail;
+    int c = -1;
+    bool more = true;
+    for (;;) {
+        if (more) {
+            const unsigned idle = __ballot_sync(0xffffffffu, c < 0);
+            if (idle) {
+                const int leader = __ffs(idle) - 1;
+                int base = 0;
+                if ((int)lane == leader) base = atomicAdd(&S.head, __popc(idle));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (c < 0) {
+                    const int i = base + __popc(idle & below);
+                    if (i < nst) c = S.qp[i];
+                }
+                if (base + __popc(idle) >= nst) more = false;
+            }
+        }
+        if (!__any_sync(0xffffffffu, c >= 0)) break;
+        if (c < 0) continue;
+        const int ly = c / SX, lx = c - ly * SX;
+        const int r = (ly + 1) * SRX + lx + 1;
+        uint32_t fl = S.pk[c] & (kPoison | kUp);
+        df v = df_make(0.0f);
+        unsigned long long a = 0;
+        if constexpr (W) v = df{S.hi[c], S.lo[c]};
+        if constexpr (AREA) a = S.ar[c];
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            const int j = r + offy(k) * SRX + offx(k);
+            const uint8_t cj = S.cg[j];
+            if ((cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && in_ext(lx + offx(k), ly + offy(k), g)) {
+                const int lj = c + offy(k) * SX + offx(k);
+                fl |= S.pk[lj] & (kPoison | kUp);
+                if constexpr (W) v = df_add(v, df{S.hi[lj], S.lo[lj]});
+                if constexpr (AREA) a += S.ar[lj];
+            }
+        }
+        if constexpr (W) {
+            S.hi[c] = v.hi;
+            S.lo[c] = v.lo;
+        }
+        if constexpr (AREA) S.ar[c] = a;
+        const uint8_t cc = S.cg[r];
+        int next = -1;
+        const int k = cc & 15;
+        if (k < 8) {
+            const int t = r + offy(k) * SRX + offx(k);
+            if ((S.cg[t] & kGlob) && in_ext(lx + offx(k), ly + offy(k), g)) {
+                const int lt = c + offy(k) * SX + offx(k);
+                // release this cell's value and flags; acquire the other donors'
+                __threadfence_block();
+                S.pk[c] = fl | kFin;
+                cuda::atomic_ref<uint32_t, cuda::thread_scope_block> at(S.pk[lt]);
+                const uint32_t old = at.fetch_sub(1u, cuda::memory_order_acq_rel);
+                if ((old & 15u) == 1u) next = lt;
+            } else {
+                S.pk[c] = fl | kFin;
+            }
+        } else {
+            S.pk[c] = fl | kFin;
+        }
+        c = next;
+    }
+}
+
+// Tiles holding at least one global cell, listed once per call (one warp per
+// tile reads the tile's rows of the global-cell bits).
+__global__ void __launch_bounds__(256) k_skel_tiles(Prob P, EngineGlobals* G, int64_t ntiles) {
+    if (__ldcg(&G->glist_count) < P.skel_min) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < ntiles; t += warps) {
+        const TileGeo g = tile_geo(P, t);
+        uint32_t any = 0;
+        for (int ly = lane; ly < g.ey; ly += 32) {
+            const int64_t b0 = (g.y0 + ly) * P.nx + g.x0, b1 = b0 + g.ex;  // bits [b0, b1)
+            for (int64_t wd = b0 >> 5; wd <= (b1 - 1) >> 5; ++wd) {
+                uint32_t m = __ldg(P.gbits + wd);
+                const int64_t lo = wd << 5;
+                if (b0 > lo) m &= ~0u << (b0 - lo);
+                if (b1 < lo + 32) m &= (1u << (b1 - lo)) - 1u;
+                any |= m;
+            }
+        }
+        if (__any_sync(0xffffffffu, any != 0) && lane == 0) {
+            const unsigned long long slot = atomicAdd(&G->skel_tiles, 1ull);
+            P.sktiles[slot] = (uint32_t)t;
+        }
+    }
+}
+
+// Pass A: in-tile partial values, exits, entries and dependency lists.
+template <bool W, bool AREA>
+__global__ void __launch_bounds__(kSkNT) k_skel_a(Prob P, EngineGlobals* G) {
+    using Sm = SmemSk<W, AREA>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sm& S = *reinterpret_cast<Sm*>(smem_raw);
+    if (__ldcg(&G->glist_count) < P.skel_min) return;
+    const unsigned long long ntl = __ldcg(&G->skel_tiles);
+    const int tid = threadIdx.x;
+    for (unsigned long long it = blockIdx.x; it < ntl; it += gridDim.x) {
+        const int64_t t = (int64_t)__ldcg(P.sktiles + it);
+        const TileGeo g = tile_geo(P, t);
+        __syncthreads();  // the previous tile's shared memory is no longer read
+        if (tid == 0) {
+            S.qtail = 0;
+            S.head = 0;
+        }
+        load_ring(S, P, g);
+        // ---- start values: rain (or 1) plus the final values of non-global
+        // donors in code order; in-tile global donors counted
+        for (int c0 = 0; c0 < SN; c0 += kSkNT) {
+            const int c = c0 + tid;
+            int start = -1;
+            const int ly = c / SX, lx = c - ly * SX;
+            const int r = (ly + 1) * SRX + lx + 1;
+            if (lx < g.ex && ly < g.ey && (S.cg[r] & kGlob)) {
+                const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
+                df v = df_make(0.0f);
+                if constexpr (W) v = df_make(P.init ? rd_in(P.init, P, gi, 8) : 1.0f);
+                unsigned long long a = 1;
+                uint32_t nin = 0;
+#pragma unroll 1
+                for (int k = 0; k < 8; ++k) {
+                    const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
+                    if ((cj & 15u) != (uint8_t)opp(k)) continue;
+                    if (cj & kGlob) {
+                        nin += in_ext(lx + offx(k), ly + offy(k), g);
+                        continue;
+                    }
+                    const int64_t gj = gi + offi(k, P.nx);
+                    if constexpr (W) v = df_add(v, df{rd_in(P.out_hi, P, gj, 30), rd_in(P.out_lo, P, gj, 31)});
+                    if constexpr (AREA) a += (unsigned long long)__ldg(P.area + gj);
+                }
+                if constexpr (W) {
+                    S.hi[c] = v.hi;
+                    S.lo[c] = v.lo;
+                }
+                if constexpr (AREA) S.ar[c] = a;
+                S.pk[c] = nin;
+                if (nin == 0) start = c;
+            }
+            push_start(S, start);
+        }
+        __syncthreads();
+        tile_walk<W, AREA>(S, g);
+        __syncthreads();
+        // ---- pointer doubling: every global cell learns where its in-tile
+        // path ends (an exit, or a cell whose receiver is none / not global)
+        for (int c = tid; c < SN; c += kSkNT) {
+            const int ly = c / SX, lx = c - ly * SX;
+            const int r = (ly + 1) * SRX + lx + 1;
+            uint16_t p = (uint16_t)(c | kPtrFinal);
+            if (lx < g.ex && ly < g.ey && (S.cg[r] & kGlob)) {
+                const int k = S.cg[r] & 15;
+                if (k < 8 && (S.cg[r + offy(k) * SRX + offx(k)] & kGlob)) {
+                    if (in_ext(lx + offx(k), ly + offy(k), g)) p = (uint16_t)(c + offy(k) * SX + offx(k));
+                    else p = (uint16_t)(c | kPtrFinal | kPtrExit);
+                }
+            }
+            S.qp[c] = p;
+        }
+        for (int round = 0; round < 13; ++round) {
+            __syncthreads();
+            int changed = 0;
+            for (int c = tid; c < SN; c += kSkNT) {
+                const uint16_t p = S.qp[c];
+                if (p & kPtrFinal) continue;
+                const uint16_t q = S.qp[p & 0xFFF];
+                S.qp[c] = (q & kPtrFinal) ? q : (uint16_t)(q & 0xFFF);
+                changed = 1;
+            }
+            if (!__syncthreads_or(changed)) break;
+        }
+        __syncthreads();
+        // ---- dependency lists (warp 0): entries in row-major boundary order;
+        // an entry's donors in other tiles take consecutive slots of the list
+        // of the exit its path reaches, in code order
+        const int nb = nboundary(g.ex, g.ey);
+        if (tid < 32) {
+            const unsigned lane = tid;
+            for (int b = lane; b < SX * 4; b += 32) S.bslots[b] = 0;
+            __syncwarp();
+            for (int b0 = 0; b0 < nb; b0 += 32) {
+                const int b = b0 + lane;
+                int x = -1, nd = 0;
+                if (b < nb) {
+                    int lx, ly;
+                    bcell(b, g.ex, g.ey, lx, ly);
+                    const int c = ly * SX + lx, r = (ly + 1) * SRX + lx + 1;
+                    if (S.cg[r] & kGlob) {
+                        for (int k = 0; k < 8; ++k) {
+                            const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
+                            nd += (cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) &&
+                                  !in_ext(lx + offx(k), ly + offy(k), g);
+                        }
+                        const uint16_t p = S.qp[c];
+                        if (nd && (p & kPtrFinal) && (p & kPtrExit)) {
+                            const int xc = p & 0xFFF;
+                            x = bindex(xc - (xc / SX) * SX, xc / SX, g.ex, g.ey);
+                        }
+                    }
+                }
+                S.wtmp[lane] = (uint8_t)nd;
+                __syncwarp();
+                const unsigned peers = __match_any_sync(0xffffffffu, x);
+                if (x >= 0) {
+                    int off = 0, tot = 0;
+                    for (unsigned m = peers; m; m &= m - 1) {
+                        const int l = __ffs(m) - 1;
+                        if (l < (int)lane) off += S.wtmp[l];
+                        tot += S.wtmp[l];
+                    }
+                    const int base = S.bslots[x];
+                    S.brank[b] = (uint16_t)(base + off);
+                    __syncwarp(peers);
+                    if ((int)lane == __ffs(peers) - 1) S.bslots[x] = (uint16_t)(base + tot);
+                }
+                __syncwarp();
+            }
+            // list begins: exclusive scan over boundary cells in order
+            int run = 0;
+            for (int b0 = 0; b0 < nb; b0 += 32) {
+                const int b = b0 + lane;
+                const int v = b < nb ? S.bslots[b] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)lane >= o) incl += u;
+                }
+                if (b < nb) S.bbeg[b] = (uint16_t)(run + incl - v);
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        __syncthreads();
+        // ---- link words, dependency slots, walker starts (one thread per boundary cell)
+        uint16_t* pool = P.skpool + t * kSkelPool;
+        for (int b = tid; b < nb; b += kSkNT) {
+            int lx, ly;
+            bcell(b, g.ex, g.ey, lx, ly);
+            const int c = ly * SX + lx, r = (ly + 1) * SRX + lx + 1;
+            if (!(S.cg[r] & kGlob)) continue;
+            const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
+            const uint16_t p = S.qp[c];
+            const bool exit = (p & kPtrExit) && (p & 0xFFF) == c;
+            int nd = 0;
+            for (int k = 0; k < 8; ++k) {
+                const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
+                nd += (cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && !in_ext(lx + offx(k), ly + offy(k), g);
+            }
+            if (exit) {
+                const unsigned long long len = S.bslots[b];
+                const bool fin = (S.pk[c] & kFin) != 0;
+                const unsigned long long pend = fin ? len : kLkNever;
+                P.link[gi] = (int64_t)(kLkExit | pend | ((unsigned long long)S.bbeg[b] << 16) | (len << 32));
+                if (fin && len == 0) {
+                    const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
+                    P.skstarts[slot] = (unsigned long long)gi;
+                }
+            } else if (nd) {
+                const bool to_exit = (p & kPtrFinal) && (p & kPtrExit);
+                unsigned long long rec = 0;
+                if (to_exit) {
+                    const int xc = p & 0xFFF;
+                    rec = kLkEntry | (unsigned long long)((g.y0 + xc / SX) * P.nx + g.x0 + (xc - (xc / SX) * SX));
+                }
+                P.link[gi] = (int64_t)rec;
+            }
+            if (nd && (p & kPtrFinal) && (p & kPtrExit)) {
+                const int xc = p & 0xFFF;
+                const int xb = bindex(xc - (xc / SX) * SX, xc / SX, g.ex, g.ey);
+                int s = S.bbeg[xb] + S.brank[b];
+                for (int k = 0; k < 8; ++k) {
+                    const int j = r + offy(k) * SRX + offx(k);
+                    const uint8_t cj = S.cg[j];
+                    if ((cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && !in_ext(lx + offx(k), ly + offy(k), g))
+                        if (FR_OK(s, kSkelPool, 32)) pool[s++] = (uint16_t)j;
+                }
+            }
+        }
+        // ---- in-tile partial values of the finished global cells
+        for (int c = tid; c < SN; c += kSkNT) {
+            const int ly = c / SX, lx = c - ly * SX;
+            if (lx >= g.ex || ly >= g.ey) continue;
+            if (!(S.cg[(ly + 1) * SRX + lx + 1] & kGlob) || !(S.pk[c] & kFin)) continue;
+            const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
+            if constexpr (W) {
+                wr_f(P.out_hi, P, gi, S.hi[c], 33);
+                wr_f(P.out_lo, P, gi, S.lo[c], 34);
+            }
+            if constexpr (AREA) wr_area(P, gi, S.ar[c]);
+        }
+    }
+}
+
+// Pass B: walkers over the exits.
+template <bool W, bool AREA>
+__global__ void __launch_bounds__(256) k_skel_walk(Prob P, EngineGlobals* G) {
+    if (__ldcg(&G->glist_count) < P.skel_min) return;
+    const unsigned long long count = __ldcg(&G->fcount[0]);
+    const int tiles_x = (int)((P.nx + SX - 1) / SX);
+    uint8_t* done = reinterpret_cast<uint8_t*>(P.cnt);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        int64_t x = (int64_t)__ldcg(P.skstarts + i);
+        for (;;) {
+            const uint8_t k = rd_rb(P, x);
+            const unsigned long long rec = (unsigned long long)__ldcg(
+                reinterpret_cast<const unsigned long long*>(P.link) + x);
+            const int begin = (int)((rec >> 16) & 0xFFFF), len = (int)((rec >> 32) & 0xFFFF);
+            const int64_t yy = x / P.nx, xx = x - yy * P.nx;
+            const int64_t tx = xx / SX, ty = yy / SY;
+            const int64_t ox = tx * SX - 1, oy = ty * SY - 1;  // ring origin of x's tile
+            const uint16_t* pool = P.skpool + (ty * tiles_x + tx) * kSkelPool;
+            df v = df_make(0.0f);
+            unsigned long long a = 0;
+            if constexpr (W) v = df{rd_cg(P.out_hi, P, x, 35), rd_cg(P.out_lo, P, x, 36)};
+            if constexpr (AREA) a = rd_area(P, x);
+#pragma unroll 1
+            for (int s = 0; s < len; ++s) {
+                const int j = __ldcg(pool + begin + s);
+                const int ry = j / SRX, rx = j - ry * SRX;
+                const int64_t y = (oy + ry) * P.nx + (ox + rx);
+                if constexpr (W) v = df_add(v, df{rd_cg(P.out_hi, P, y, 37), rd_cg(P.out_lo, P, y, 38)});
+                if constexpr (AREA) a += rd_area(P, y);
+            }
+            if constexpr (W) {
+                wr_f(P.out_hi, P, x, v.hi, 39);
+                wr_f(P.out_lo, P, x, v.lo, 40);
+            }
+            if constexpr (AREA) wr_area(P, x, a);
+            if (FR_OK(x, ncell(P), 41)) done[x] = 1;
+            // the exit reached from this exit's receiver (an entry of the next tile)
+            if (k >= 8) break;
+            const int64_t s = x + offi(k, P.nx);
+            const unsigned long long rs = (unsigned long long)__ldcg(
+                reinterpret_cast<const unsigned long long*>(P.link) + s);
+            int64_t q;
+            if ((rs & kLkKind) == kLkExit) q = s;
+            else if ((rs & kLkKind) == kLkEntry) q = (int64_t)(rs & kLkCell);
+            else break;
+            if (!FR_OK(q, ncell(P), 42)) break;
+            // release this exit's value; the completing arrival acquires all
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> at(
+                reinterpret_cast<unsigned long long*>(P.link)[q]);
+            const unsigned long long old = at.fetch_sub(1ull, cuda::memory_order_acq_rel);
+            if ((old & 0xFFFFull) != 1ull) break;
+            x = q;
+        }
+    }
+}
+
+// Pass C: inflows of the entries passed down the in-tile receivers; final
+// values of the global cells; completion count.
+template <bool W, bool AREA>
+__global__ void __launch_bounds__(kSkNT) k_skel_fix(Prob P, EngineGlobals* G,
+                                                   unsigned long long total_cells) {
+    using Sm = SmemSk<W, AREA>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sm& S = *reinterpret_cast<Sm*>(smem_raw);
+    if (__ldcg(&G->glist_count) < P.skel_min) return;
+    const unsigned long long ntl = __ldcg(&G->skel_tiles);
+    const uint8_t* done_b = reinterpret_cast<const uint8_t*>(P.cnt);
+    const int tid = threadIdx.x;
+    unsigned long long done = 0;
+    for (unsigned long long it = blockIdx.x; it < ntl; it += gridDim.x) {
+        const int64_t t = (int64_t)__ldcg(P.sktiles + it);
+        const TileGeo g = tile_geo(P, t);
+        __syncthreads();
+        if (tid == 0) {
+            S.qtail = 0;
+            S.head = 0;
+        }
+        load_ring(S, P, g);
+        for (int c0 = 0; c0 < SN; c0 += kSkNT) {
+            const int c = c0 + tid;
+            int start = -1;
+            const int ly = c / SX, lx = c - ly * SX;
+            const int r = (ly + 1) * SRX + lx + 1;
+            if (lx < g.ex && ly < g.ey && (S.cg[r] & kGlob)) {
+                const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
+                df v = df_make(0.0f);
+                unsigned long long a = 0;
+                uint32_t nin = 0, fl = 0;
+#pragma unroll 1
+                for (int k = 0; k < 8; ++k) {
+                    const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
+                    if (!(cj & kGlob) || (cj & 15u) != (uint8_t)opp(k)) continue;
+                    if (in_ext(lx + offx(k), ly + offy(k), g)) {
+                        ++nin;
+                        continue;
+                    }
+                    // a donor in another tile: an exit, final after pass B
+                    const int64_t gj = gi + offi(k, P.nx);
+                    fl |= kUp;
+                    if (!done_b[gj]) fl |= kPoison;
+                    if constexpr (W) v = df_add(v, df{rd_cg(P.out_hi, P, gj, 43), rd_cg(P.out_lo, P, gj, 44)});
+                    if constexpr (AREA) a += rd_area(P, gj);
+                }
+                if constexpr (W) {
+                    S.hi[c] = v.hi;
+                    S.lo[c] = v.lo;
+                }
+                if constexpr (AREA) S.ar[c] = a;
+                S.pk[c] = nin | fl;
+                if (nin == 0) start = c;
+            }
+            push_start(S, start);
+        }
+        __syncthreads();
+        tile_walk<W, AREA>(S, g);
+        __syncthreads();
+        for (int c = tid; c < SN; c += kSkNT) {
+            const int ly = c / SX, lx = c - ly * SX;
+            const int r = (ly + 1) * SRX + lx + 1;
+            if (lx >= g.ex || ly >= g.ey || !(S.cg[r] & kGlob)) continue;
+            const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
+            const int k = S.cg[r] & 15;
+            const bool exit = k < 8 && (S.cg[r + offy(k) * SRX + offx(k)] & kGlob) &&
+                              !in_ext(lx + offx(k), ly + offy(k), g);
+            if (exit) {
+                done += done_b[gi] ? 1 : 0;
+                continue;
+            }
+            const uint32_t pkc = S.pk[c];
+            if (!(pkc & kFin) || (pkc & kPoison)) continue;
+            ++done;
+            if (!(pkc & kUp)) continue;  // no inflow from other tiles: L is final
+            if constexpr (W) {
+                const df v = df_add(df{rd_cg(P.out_hi, P, gi, 45), rd_cg(P.out_lo, P, gi, 46)},
+                                    df{S.hi[c], S.lo[c]});
+                wr_f(P.out_hi, P, gi, v.hi, 47);
+                wr_f(P.out_lo, P, gi, v.lo, 48);
+            }
+            if constexpr (AREA) wr_area(P, gi, rd_area(P, gi) + S.ar[c]);
+        }
+    }
+    // completion count; the last CTA checks that every cell was computed
+    __shared__ unsigned long long s_done;
+    for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
+    __syncthreads();
+    if (tid == 0) s_done = 0;
+    __syncthreads();
+    if ((tid & 31) == 0 && done) atomicAdd(&s_done, done);
+    __syncthreads();
+    if (tid == 0) {
+        if (s_done) atomicAdd(&G->done_cells, s_done);
+        __threadfence();
+        const unsigned fin = atomicAdd(&G->finished_ctas, 1u);
+        if (fin == gridDim.x - 1) {
+            __threadfence();
+            const unsigned long long got = atomicAdd(&G->done_cells, 0ull);
+            if (got != total_cells) atomicMax(&G->status, kStatusNoProgress);
+        }
+    }
+}
+
+template <class K>
+int persistent_grid(K kernel, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kSkNT, smem) != cudaSuccess) return 0;
+    return sms * (per > 0 ? per : 1);
+}
+
+template <bool W, bool AREA>
+cudaError_t launch_skel_t(const Prob& P, EngineGlobals* G, cudaStream_t s) {
+    constexpr size_t sm = sizeof(SmemSk<W, AREA>);
+    static std::atomic<unsigned long long> set_a{0}, set_c{0};
+    static int grid_a = 0, grid_c = 0;
+    cudaError_t e = smem_limit_once(k_skel_a<W, AREA>, sm, set_a);
+    if (e != cudaSuccess) return e;
+    e = smem_limit_once(k_skel_fix<W, AREA>, sm, set_c);
+    if (e != cudaSuccess) return e;
+    if (!grid_a) grid_a = persistent_grid(k_skel_a<W, AREA>, sm);
+    if (!grid_c) grid_c = persistent_grid(k_skel_fix<W, AREA>, sm);
+    if (!grid_a || !grid_c) return cudaErrorInvalidConfiguration;
+    const int64_t ntiles = skel_tiles(P.nx, P.ny);
+    int tgrid = (int)((ntiles + 7) / 8);
+    if (tgrid > 16 * 152) tgrid = 16 * 152;
+    if (tgrid < 1) tgrid = 1;
+    k_skel_tiles<<<tgrid, 256, 0, s>>>(P, G, ntiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_skel_a<W, AREA><<<grid_a, kSkNT, sm, s>>>(P, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_skel_walk<W, AREA><<<walker_grid(), 256, 0, s>>>(P, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_skel_fix<W, AREA><<<grid_c, kSkNT, sm, s>>>(P, G, (unsigned long long)(P.nx * P.ny));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_d8_skeleton(bool want_w, bool want_area, const Prob& P, EngineGlobals* G,
+                               cudaStream_t s) {
+    if (want_w && want_area) return launch_skel_t<true, true>(P, G, s);
+    if (want_w) return launch_skel_t<true, false>(P, G, s);
+    return launch_skel_t<false, true>(P, G, s);
+}
+
+}  // namespace fr
