@@ -72,10 +72,12 @@ struct SmemD8 {
     alignas(16) uint32_t pk[NR];                  // packed arrivals / donors' area
     alignas(16) uint8_t code[NR];                 // receiver codes of region + ring, padded rows
     alignas(16) uint8_t dm[W ? NR : 16];          // donor masks (value pulls)
-    uint16_t queue[Gm::NE];                       // ready list: cells whose donors (all leaves) finished in the leaf pass
+    uint16_t queue[Gm::NE];                       // ready list: cells whose donors (all leaves) finished in the
+                                                  // leaf pass; after the walk, the inner tile's unfinished cells
     int qtail;                                    // its length
     int head;                                     // next entry to hand out
-    unsigned long long done;
+    int nglob;                                    // unfinished inner cells listed in queue after the walk
+    unsigned long long done, gbase;
 };
 
 // Warp-aggregated append of four optional cells per lane (-1: none; all lanes
@@ -162,12 +164,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Marks one global inner cell (rare): its bit and a list entry.
-__device__ __forceinline__ void mark_one(const Prob& P, EngineGlobals* G, int64_t gi, int pid) {
-    atomicOr(P.gbits + (gi >> 5), 1u << (gi & 31));
-    const unsigned long long slot = atomicAdd(&G->glist_count, 1ull);
-    if (FR_OK((int64_t)slot, P.glist_cap, 17))
-        P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
+// Lists the block's unfinished inner cells (local indices in S.queue, S.nglob
+// of them) as global: one list allocation per block, their bits or-ed once
+// per word and warp.  Called by all threads after a barrier.
+template <class S_>
+__device__ __forceinline__ void list_global(S_& S, const Prob& P, EngineGlobals* G, int pid,
+                                            int tx_inner, int64_t x0, int64_t y0, int nthreads) {
+    const int ng = S.nglob;
+    if (threadIdx.x == 0) S.gbase = atomicAdd(&G->glist_count, (unsigned long long)ng);
+    __syncthreads();
+    const unsigned long long base = S.gbase;
+    const int ng32 = (ng + 31) & ~31;
+    for (int i = threadIdx.x; i < ng32; i += nthreads) {
+        int64_t gi = -1;
+        if (i < ng) {
+            const int c = S.queue[i];
+            const int ly = c / tx_inner, lx = c - ly * tx_inner;
+            gi = (y0 + ly) * P.nx + x0 + lx;
+            if (FR_OK((int64_t)(base + i), P.glist_cap, 17))
+                P.glist[base + i] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
+        }
+        // lanes whose cells share a word of bits or them together; one atomic per word
+        const long long word = gi >= 0 ? (long long)(gi >> 5) : -1ll;
+        const unsigned peers = __match_any_sync(0xffffffffu, word);
+        const uint32_t bits = __reduce_or_sync(peers, gi >= 0 ? 1u << (gi & 31) : 0u);
+        if (gi >= 0 && (int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicOr(P.gbits + word, bits);
+    }
 }
 
 // Problem and tile of this CTA: one problem, or (batched) the problem whose
@@ -233,6 +255,7 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
     if (tid == 0) {
         S.qtail = 0;
         S.head = 0;
+        S.nglob = 0;
     }
 
     if (vec) {
@@ -448,6 +471,8 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
         if (lxr < 0 || lyr < 0 || lxr >= TX || lyr >= TY) return true;
         return !pk_final(S.pk[r + offy(k) * CP + offx(k)]);
     };
+    // an unfinished cell is appended to the block's list (S.queue, S.nglob)
+    // and listed as global after the loops
     auto publish_one = [&](int lx, int ly) {
         const int64_t gx = x0 + lx, gy = y0 + ly;
         if (gx >= P.nx || gy >= P.ny) return;
@@ -455,7 +480,7 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
         const int64_t gi = gy * P.nx + gx;
         const uint32_t pkc = S.pk[r];
         if (!pk_final(pkc)) {
-            mark_one(P, G, gi, pid);
+            S.queue[atomicAdd(&S.nglob, 1)] = (uint16_t)(ly * TX + lx);
             return;
         }
         ++done;
@@ -502,6 +527,7 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
     if ((tid & 31) == 0 && done) atomicAdd(&S.done, done);
     __syncthreads();
     if (tid == 0 && S.done) atomicAdd(&G->done_cells, S.done);
+    if (S.nglob) list_global(S, P, G, pid, TX, x0, y0, NT8);
 }
 
 template <class Gm, bool W, bool AREA, bool BATCH>

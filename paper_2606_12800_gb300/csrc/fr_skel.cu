@@ -55,11 +55,19 @@ static_assert(kSkelPool == 2 * (SX + SY) + 4, "dependency slots per tile: the ri
 // for receivers outside the grid) and the global flag.
 constexpr uint8_t kNoCode = 15, kGlob = 0x80;
 
-// Per-cell word of the in-tile walkers: pending in-tile global donors
-// (bits 0-3) and flags.
+// In-tile walker words.  Areas alone (push): one 64-bit word per cell, a
+// count in bits 56-63 that reaches kDone when the cell is final (its preset
+// adds kDone - in-tile global donors, at least one; every donor adds one),
+// an inflow-poison count in bits 48-55 and the value in bits 0-47, to which
+// each donor adds its own: integer adds commute, so no value needs a fence.
+// Two-float values (pull): a 32-bit word with the pending count (bits 0-3)
+// and flags; a final cell pulls its donors' values in code order.
+constexpr unsigned long long kPwOne = 1ull << 56, kPwPois = 1ull << 48, kPwVal = (1ull << 48) - 1;
+constexpr unsigned kDone = 9;
 constexpr uint32_t kFin = 1u << 31, kPoison = 1u << 30, kUp = 1u << 29;
-// Pointer-doubling word: a local index (bits 0-11), final (bit 12: the path
-// ends here), exit (bit 13: ... by leaving the tile).
+// Successor word of a global cell: its in-tile global receiver (local index,
+// bits 0-11), or the cell itself with kPtrFinal set when its in-tile path
+// ends there, and kPtrExit when it ends by leaving the tile.
 constexpr uint16_t kPtrFinal = 1u << 12, kPtrExit = 1u << 13;
 
 // Link word of a boundary cell (per cell, 8 bytes, in the workspace):
@@ -120,47 +128,139 @@ __device__ __forceinline__ int bindex(int lx, int ly, int ex, int ey) {
 
 template <bool W, bool AREA>
 struct SmemSk {
-    uint8_t cg[SRN];                        // ring layout: code | kGlob
-    alignas(16) uint32_t pk[SN];            // walker words (inner cells)
-    uint16_t qp[SN];                        // walker start list, then pointer doubling
-    float hi[W ? SN : 1], lo[W ? SN : 1];   // two-float values (L in A, inflow sums in C)
-    unsigned long long ar[AREA ? SN : 1];   // areas
-    uint16_t bslots[SX * 4];                // per boundary cell: dependency slots (exits: list length)
-    uint16_t bbeg[SX * 4];                  // per exit: list begin
-    uint16_t brank[SX * 4];                 // per entry: offset in its exit's list
-    uint8_t wtmp[32];                       // warp-0 scratch
-    int qtail, head, tile_ok;
-    unsigned long long done;
+    static constexpr bool kPush = AREA && !W;
+    uint8_t cg[SRN];                                    // ring layout: code | kGlob
+    uint8_t dm[kPush ? 1 : SN];                         // pull: in-tile global donors (codes)
+    alignas(16) unsigned long long pw[kPush ? SN : 1];  // push: count | poison | value
+    uint32_t pk[kPush ? 1 : SN];                        // pull: pending count | flags
+    float hi[W ? SN : 1], lo[W ? SN : 1];               // pull: two-float values
+    unsigned long long ar[(W && AREA) ? SN : 1];        // pull: areas beside the water
+    uint16_t qp[SN];                                    // walker start list
+    uint16_t sc[SN];                                    // successor words of the global cells
+    uint8_t nin[SN];                                    // in-tile global donors of each global cell
+    uint16_t gl[SN];                                    // the tile's global cells, row-major
+    uint16_t broot[SX * 4];                             // per boundary cell: end of its in-tile path
+    uint16_t bslots[SX * 4];                            // per boundary cell: dependency slots (exits: list length)
+    uint16_t bbeg[SX * 4];                              // per exit: list begin
+    uint16_t brank[SX * 4];                             // per entry: offset in its exit's list
+    int bdep[SX * 4];                                   // push: per exit, its dependencies
+    uint8_t bnd[SX * 4];                                // per boundary cell: global donors in other tiles
+    unsigned long long bval[SX * 4];                    // pass C: entry inflow (push: value | poison;
+    float bhi[W ? SX * 4 : 1], blo[W ? SX * 4 : 1];     //   pull: two-float, areas, flags)
+    uint32_t bfl[SX * 4];
+    uint8_t wtmp[32];                                   // warp-0 scratch
+    int wsum[kSkNT / 32];                               // block scan
+    int qtail, head, ng;
 };
 
 __device__ __forceinline__ bool in_ext(int lx, int ly, const TileGeo& g) {
     return lx >= 0 && ly >= 0 && lx < g.ex && ly < g.ey;
 }
 
-// Loads the receiver codes and global flags of a tile and its ring.  Returns
-// (block-uniform) whether the tile holds a global cell.
+// Loads the receiver codes and global flags of a tile and its ring (all
+// loads issued before any is used), then lists the tile's global cells in
+// row-major order (S.gl, S.ng).
 template <class S_>
-__device__ bool load_ring(S_& S, const Prob& P, const TileGeo& g) {
-    int any = 0;
-    for (int i = threadIdx.x; i < SRN; i += kSkNT) {
+__device__ void load_tile(S_& S, const Prob& P, const TileGeo& g) {
+    // interior tiles of a grid whose rows are 32-cell aligned: 16-byte code
+    // chunks and one word of global bits per chunk (grid x in [x0 - 16, x0 + 80))
+    if (g.ex == SX && g.ey == SY && (P.nx & 31) == 0 && ((uintptr_t)P.rb & 15) == 0 && g.x0 >= 16 &&
+        g.x0 + SX + 16 <= P.nx && g.y0 >= 1 && g.y0 + SY + 1 <= P.ny) {
+        constexpr int CH = (SX + 32) / 16, NCH = SRY * CH;
+        constexpr int PER2 = (NCH + kSkNT - 1) / kSkNT;
+        uint4 cv[PER2];
+        uint32_t bw[PER2];
+#pragma unroll
+        for (int q = 0; q < PER2; ++q) {
+            const int i = threadIdx.x + q * kSkNT;
+            cv[q] = make_uint4(0, 0, 0, 0);
+            bw[q] = 0;
+            if (i < NCH) {
+                const int ry = i / CH, ch = i - ry * CH;
+                const int64_t g0 = (g.y0 - 1 + ry) * P.nx + g.x0 - 16 + 16 * ch;
+                cv[q] = __ldg(reinterpret_cast<const uint4*>(P.rb + g0));
+                bw[q] = __ldg(P.gbits + (g0 >> 5)) >> (g0 & 31);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER2; ++q) {
+            const int i = threadIdx.x + q * kSkNT;
+            if (i >= NCH) break;
+            const int ry = i / CH, ch = i - ry * CH;
+            const uint32_t w4[4] = {cv[q].x, cv[q].y, cv[q].z, cv[q].w};
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int rx = 16 * ch - 15 + j;  // ring column of grid x0 - 16 + 16 ch + j
+                if (rx < 0 || rx >= SRX) continue;
+                const uint32_t k = (w4[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+                // interior tile: every ring cell's receiver lies in the grid
+                S.cg[ry * SRX + rx] = (uint8_t)((k < 8 ? k : kNoCode) | (((bw[q] >> j) & 1u) ? kGlob : 0u));
+            }
+        }
+    } else {
+    constexpr int PER = (SRN + kSkNT - 1) / kSkNT;
+    uint8_t kb[PER];
+    uint32_t gw[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x + q * kSkNT;
+        const int ry = i / SRX, rx = i - ry * SRX;
+        const int64_t gx = g.x0 - 1 + rx, gy = g.y0 - 1 + ry;
+        kb[q] = 0xFF;
+        gw[q] = 0;
+        if (i < SRN && gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
+            const int64_t gi = gy * P.nx + gx;
+            kb[q] = rd_rb(P, gi);
+            gw[q] = __ldg(P.gbits + (gi >> 5)) >> (gi & 31);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x + q * kSkNT;
+        if (i >= SRN) break;
         const int ry = i / SRX, rx = i - ry * SRX;
         const int64_t gx = g.x0 - 1 + rx, gy = g.y0 - 1 + ry;
         uint8_t c = kNoCode;
-        if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
-            const int64_t gi = gy * P.nx + gx;
-            const uint8_t k = rd_rb(P, gi);
-            if (k < 8) {
-                const int64_t tx = gx + offx(k), ty = gy + offy(k);
-                if (tx >= 0 && ty >= 0 && tx < P.nx && ty < P.ny) c = k;
-            }
-            if (gbit(P, gi)) {
-                c |= kGlob;
-                if (rx >= 1 && ry >= 1 && rx <= g.ex && ry <= g.ey) any = 1;
-            }
+        const uint32_t k = kb[q];
+        if (k < 8) {
+            const int64_t tx = gx + offx(k), ty = gy + offy(k);
+            if (tx >= 0 && ty >= 0 && tx < P.nx && ty < P.ny) c = (uint8_t)k;
         }
+        if (gw[q] & 1u) c |= kGlob;
         S.cg[i] = c;
     }
-    return __syncthreads_or(any) != 0;
+    }
+    __syncthreads();
+    // compact list: thread t takes cells [CPT t, CPT t + CPT)
+    constexpr int CPT = SN / kSkNT;
+    static_assert(CPT * kSkNT == SN && CPT <= 32, "cells per thread");
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+        const int c = threadIdx.x * CPT + j;
+        const int ly = c / SX, lx = c - ly * SX;
+        if (lx < g.ex && ly < g.ey && (S.cg[(ly + 1) * SRX + lx + 1] & kGlob)) m |= 1u << j;
+    }
+    const unsigned lane = threadIdx.x & 31u;
+    const int cnt = __popc(m);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += u;
+    }
+    if (lane == 31) S.wsum[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    int off = incl - cnt, total = 0;
+#pragma unroll
+    for (int w = 0; w < kSkNT / 32; ++w) {
+        const int v = S.wsum[w];
+        if (w < (int)(threadIdx.x >> 5)) off += v;
+        total += v;
+    }
+    for (uint32_t mm = m; mm; mm &= mm - 1) S.gl[off++] = (uint16_t)(threadIdx.x * CPT + __ffs(mm) - 1);
+    if (threadIdx.x == 0) S.ng = total;
+    __syncthreads();
 }
 
 // Warp-aggregated append of one optional local cell per lane (all lanes call).
@@ -176,75 +276,119 @@ __device__ __forceinline__ void push_start(S_& S, int cell) {
     if (cell >= 0) S.qp[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)cell;
 }
 
-// In-tile walker solve over the global cells: a cell is finalised once its
-// in-tile global donors are (its value: its own start value plus theirs in
-// code order; flags or-ed), then arrives at its in-tile global receiver; the
-// arrival that completes the receiver's count continues there.
-template <bool W, bool AREA, class S_>
-__device__ void tile_walk(S_& S, const TileGeo& g) {
+// Warp-aggregated hand-out of the start list: returns the next start for
+// idle lanes (c < 0), -1 when none is left.
+template <class S_>
+__device__ __forceinline__ void hand_out(S_& S, int nst, int& c, bool& more) {
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned below = (1u << lane) - 1u;
+    const unsigned idle = __ballot_sync(0xffffffffu, c < 0);
+    if (!idle) return;
+    const int leader = __ffs(idle) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(&S.head, __popc(idle));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c < 0) {
+        const int i = base + __popc(idle & ((1u << lane) - 1u));
+        if (i < nst) c = S.qp[i];
+    }
+    if (base + __popc(idle) >= nst) more = false;
+}
+
+// Successor word of global cell c (local index; ring index r): its in-tile
+// global receiver, or c itself marked final (and exit if the receiver is a
+// global cell of another tile).
+__device__ __forceinline__ uint16_t succ_word(const uint8_t* cg, int c, int r, const TileGeo& g) {
+    const int ly = c / SX, lx = c - ly * SX;
+    const int k = cg[r] & 15;
+    if (k < 8 && (cg[r + offy(k) * SRX + offx(k)] & kGlob)) {
+        if (in_ext(lx + offx(k), ly + offy(k), g)) return (uint16_t)(c + offy(k) * SX + offx(k));
+        return (uint16_t)(c | kPtrFinal | kPtrExit);
+    }
+    return (uint16_t)(c | kPtrFinal);
+}
+
+// In-tile walker solve over the global cells, areas alone: a final cell
+// adds its word (one arrival, its poison flag, its value) to its in-tile
+// global receiver's; the add that completes the receiver's count continues
+// there ("last arriver continues").  The walker carries the final word.
+template <class S_>
+__device__ void walk_push(S_& S) {
+    const int nst = S.qtail;
+    int c = -1;
+    unsigned long long w = 0;
+    bool more = true;
+    for (;;) {
+        if (more) {
+            const int was = c;
+            hand_out(S, nst, c, more);
+            if (was < 0 && c >= 0) w = S.pw[c];  // a start: final at its preset
+        }
+        if (!__any_sync(0xffffffffu, c >= 0)) break;
+        if (c < 0) continue;
+        const uint16_t p = S.sc[c];
+        int next = -1;
+        if (!(p & kPtrFinal)) {
+            const int t = p;
+            const unsigned long long add = kPwOne | ((w >> 48) & 0xFFull ? kPwPois : 0ull) | (w & kPwVal);
+            if (S.nin[t] == 1) {
+                // the receiver's only in-tile donor: nothing else arrives there
+                w = S.pw[t] + add;
+                S.pw[t] = w;
+                next = t;
+            } else {
+                const unsigned long long old = atomicAdd(&S.pw[t], add);
+                if ((old >> 56) == kDone - 1) {
+                    next = t;
+                    w = old + add;
+                }
+            }
+        }
+        c = next;
+    }
+}
+
+// The same with two-float values (and areas beside them): a final cell pulls
+// its in-tile global donors' values in code order, then arrives at its
+// receiver (relaxed atomic between two fences: the donor's values are
+// written before its arrival, the completing thread reads them after).
+template <bool AREA, class S_>
+__device__ void walk_pull(S_& S) {
     const int nst = S.qtail;
     int c = -1;
     bool more = true;
     for (;;) {
-        if (more) {
-            const unsigned idle = __ballot_sync(0xffffffffu, c < 0);
-            if (idle) {
-                const int leader = __ffs(idle) - 1;
-                int base = 0;
-                if ((int)lane == leader) base = atomicAdd(&S.head, __popc(idle));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (c < 0) {
-                    const int i = base + __popc(idle & below);
-                    if (i < nst) c = S.qp[i];
-                }
-                if (base + __popc(idle) >= nst) more = false;
-            }
-        }
+        if (more) hand_out(S, nst, c, more);
         if (!__any_sync(0xffffffffu, c >= 0)) break;
         if (c < 0) continue;
-        const int ly = c / SX, lx = c - ly * SX;
-        const int r = (ly + 1) * SRX + lx + 1;
         uint32_t fl = S.pk[c] & (kPoison | kUp);
-        df v = df_make(0.0f);
+        df v = df{S.hi[c], S.lo[c]};
         unsigned long long a = 0;
-        if constexpr (W) v = df{S.hi[c], S.lo[c]};
         if constexpr (AREA) a = S.ar[c];
-#pragma unroll 1
-        for (int k = 0; k < 8; ++k) {
-            const int j = r + offy(k) * SRX + offx(k);
-            const uint8_t cj = S.cg[j];
-            if ((cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && in_ext(lx + offx(k), ly + offy(k), g)) {
-                const int lj = c + offy(k) * SX + offx(k);
-                fl |= S.pk[lj] & (kPoison | kUp);
-                if constexpr (W) v = df_add(v, df{S.hi[lj], S.lo[lj]});
-                if constexpr (AREA) a += S.ar[lj];
-            }
+        for (uint32_t m = S.dm[c]; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
+            const int lj = c + offy(k) * SX + offx(k);
+            fl |= S.pk[lj] & (kPoison | kUp);
+            v = df_add(v, df{S.hi[lj], S.lo[lj]});
+            if constexpr (AREA) a += S.ar[lj];
         }
-        if constexpr (W) {
-            S.hi[c] = v.hi;
-            S.lo[c] = v.lo;
-        }
+        S.hi[c] = v.hi;
+        S.lo[c] = v.lo;
         if constexpr (AREA) S.ar[c] = a;
-        const uint8_t cc = S.cg[r];
+        S.pk[c] = fl | kFin;
+        const uint16_t p = S.sc[c];
         int next = -1;
-        const int k = cc & 15;
-        if (k < 8) {
-            const int t = r + offy(k) * SRX + offx(k);
-            if ((S.cg[t] & kGlob) && in_ext(lx + offx(k), ly + offy(k), g)) {
-                const int lt = c + offy(k) * SX + offx(k);
-                // release this cell's value and flags; acquire the other donors'
-                __threadfence_block();
-                S.pk[c] = fl | kFin;
-                cuda::atomic_ref<uint32_t, cuda::thread_scope_block> at(S.pk[lt]);
-                const uint32_t old = at.fetch_sub(1u, cuda::memory_order_acq_rel);
-                if ((old & 15u) == 1u) next = lt;
+        if (!(p & kPtrFinal)) {
+            const int t = p;
+            if (S.nin[t] == 1) {
+                next = t;  // the receiver's only in-tile donor: continue without an arrival
             } else {
-                S.pk[c] = fl | kFin;
+                __threadfence_block();
+                const uint32_t old = atomicSub(&S.pk[t], 1u);
+                if ((old & 15u) == 1u) {
+                    __threadfence_block();
+                    next = t;
+                }
             }
-        } else {
-            S.pk[c] = fl | kFin;
         }
         c = next;
     }
@@ -278,8 +422,9 @@ __global__ void __launch_bounds__(256) k_skel_tiles(Prob P, EngineGlobals* G, in
 
 // Pass A: in-tile partial values, exits, entries and dependency lists.
 template <bool W, bool AREA>
-__global__ void __launch_bounds__(kSkNT) k_skel_a(Prob P, EngineGlobals* G) {
+__global__ void __launch_bounds__(kSkNT, 3) k_skel_a(Prob P, EngineGlobals* G) {
     using Sm = SmemSk<W, AREA>;
+    constexpr bool kPush = Sm::kPush;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm& S = *reinterpret_cast<Sm*>(smem_raw);
     if (__ldcg(&G->glist_count) < P.skel_min) return;
@@ -293,78 +438,111 @@ __global__ void __launch_bounds__(kSkNT) k_skel_a(Prob P, EngineGlobals* G) {
             S.qtail = 0;
             S.head = 0;
         }
-        load_ring(S, P, g);
+        load_tile(S, P, g);
+        const int ng = S.ng;
         // ---- start values: rain (or 1) plus the final values of non-global
         // donors in code order; in-tile global donors counted
-        for (int c0 = 0; c0 < SN; c0 += kSkNT) {
-            const int c = c0 + tid;
+        for (int i0 = 0; i0 < ng; i0 += kSkNT) {  // warp-uniform trip count
+            const int i = i0 + tid;
             int start = -1;
-            const int ly = c / SX, lx = c - ly * SX;
-            const int r = (ly + 1) * SRX + lx + 1;
-            if (lx < g.ex && ly < g.ey && (S.cg[r] & kGlob)) {
+            if (i < ng) {
+                const int c = S.gl[i];
+                const int ly = c / SX, lx = c - ly * SX;
+                const int r = (ly + 1) * SRX + lx + 1;
                 const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
-                df v = df_make(0.0f);
-                if constexpr (W) v = df_make(P.init ? rd_in(P.init, P, gi, 8) : 1.0f);
-                unsigned long long a = 1;
-                uint32_t nin = 0;
-#pragma unroll 1
+                uint32_t loc = 0, din = 0;
+#pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
                     if ((cj & 15u) != (uint8_t)opp(k)) continue;
-                    if (cj & kGlob) {
-                        nin += in_ext(lx + offx(k), ly + offy(k), g);
-                        continue;
-                    }
-                    const int64_t gj = gi + offi(k, P.nx);
-                    if constexpr (W) v = df_add(v, df{rd_in(P.out_hi, P, gj, 30), rd_in(P.out_lo, P, gj, 31)});
-                    if constexpr (AREA) a += (unsigned long long)__ldg(P.area + gj);
+                    if (!(cj & kGlob)) loc |= 1u << k;
+                    else if (in_ext(lx + offx(k), ly + offy(k), g)) din |= 1u << k;
                 }
-                if constexpr (W) {
+                df v = df_make(0.0f);
+                if constexpr (W) v = df_make(P.init ? rd_in(P.init, P, gi, 8) : 1.0f);
+                unsigned long long a = 1;
+                if (loc) {
+                    float h[8], l[8];
+                    unsigned long long av[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const bool on = (loc >> k) & 1u;
+                        const int64_t gj = gi + offi(k, P.nx);
+                        h[k] = l[k] = 0.0f;
+                        av[k] = 0;
+                        if constexpr (W) {
+                            if (on) {
+                                h[k] = rd_in(P.out_hi, P, gj, 30);
+                                l[k] = rd_in(P.out_lo, P, gj, 31);
+                            }
+                        }
+                        if constexpr (AREA) {
+                            if (on) av[k] = (unsigned long long)__ldg(P.area + gj);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (!((loc >> k) & 1u)) continue;
+                        if constexpr (W) v = df_add(v, df{h[k], l[k]});
+                        a += av[k];
+                    }
+                }
+                const uint32_t nin = __popc(din);
+                S.nin[c] = (uint8_t)nin;
+                S.sc[c] = succ_word(S.cg, c, r, g);
+                if constexpr (kPush) {
+                    S.pw[c] = (unsigned long long)(kDone - nin) << 56 | a;
+                } else {
                     S.hi[c] = v.hi;
                     S.lo[c] = v.lo;
+                    if constexpr (AREA) S.ar[c] = a;
+                    S.pk[c] = nin;
+                    S.dm[c] = (uint8_t)din;
                 }
-                if constexpr (AREA) S.ar[c] = a;
-                S.pk[c] = nin;
                 if (nin == 0) start = c;
             }
             push_start(S, start);
         }
         __syncthreads();
-        tile_walk<W, AREA>(S, g);
+        if constexpr (kPush) walk_push(S);
+        else walk_pull<AREA>(S);
         __syncthreads();
-        // ---- pointer doubling: every global cell learns where its in-tile
-        // path ends (an exit, or a cell whose receiver is none / not global)
-        for (int c = tid; c < SN; c += kSkNT) {
-            const int ly = c / SX, lx = c - ly * SX;
+        // ---- where each boundary cell's in-tile path ends (one thread per
+        // boundary cell follows the successor words; at most ng steps, so a
+        // cycle ends the walk with "no end"), and its donors in other tiles
+        const int nb = nboundary(g.ex, g.ey);
+        for (int b = tid; b < SX * 4; b += kSkNT) S.bdep[b] = 0;
+        __syncthreads();
+        for (int b = tid; b < nb; b += kSkNT) {
+            int lx, ly;
+            bcell(b, g.ex, g.ey, lx, ly);
             const int r = (ly + 1) * SRX + lx + 1;
-            uint16_t p = (uint16_t)(c | kPtrFinal);
-            if (lx < g.ex && ly < g.ey && (S.cg[r] & kGlob)) {
-                const int k = S.cg[r] & 15;
-                if (k < 8 && (S.cg[r + offy(k) * SRX + offx(k)] & kGlob)) {
-                    if (in_ext(lx + offx(k), ly + offy(k), g)) p = (uint16_t)(c + offy(k) * SX + offx(k));
-                    else p = (uint16_t)(c | kPtrFinal | kPtrExit);
+            uint16_t root = 0;
+            int nd = 0;
+            if (S.cg[r] & kGlob) {
+                uint16_t p = S.sc[ly * SX + lx];
+                for (int n = 0; n < ng && !(p & kPtrFinal); ++n) p = S.sc[p & 0xFFF];
+                root = (p & kPtrFinal) ? p : 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
+                    nd += (cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && !in_ext(lx + offx(k), ly + offy(k), g);
+                }
+                if constexpr (kPush) {
+                    if (nd && (root & kPtrExit)) {
+                        const int xc = root & 0xFFF;
+                        atomicAdd(&S.bdep[bindex(xc - (xc / SX) * SX, xc / SX, g.ex, g.ey)], nd);
+                    }
                 }
             }
-            S.qp[c] = p;
-        }
-        for (int round = 0; round < 13; ++round) {
-            __syncthreads();
-            int changed = 0;
-            for (int c = tid; c < SN; c += kSkNT) {
-                const uint16_t p = S.qp[c];
-                if (p & kPtrFinal) continue;
-                const uint16_t q = S.qp[p & 0xFFF];
-                S.qp[c] = (q & kPtrFinal) ? q : (uint16_t)(q & 0xFFF);
-                changed = 1;
-            }
-            if (!__syncthreads_or(changed)) break;
+            S.broot[b] = root;
+            S.bnd[b] = (uint8_t)nd;
         }
         __syncthreads();
         // ---- dependency lists (warp 0): entries in row-major boundary order;
         // an entry's donors in other tiles take consecutive slots of the list
         // of the exit its path reaches, in code order
-        const int nb = nboundary(g.ex, g.ey);
-        if (tid < 32) {
+        if (!kPush && tid < 32) {
             const unsigned lane = tid;
             for (int b = lane; b < SX * 4; b += 32) S.bslots[b] = 0;
             __syncwarp();
@@ -374,15 +552,11 @@ __global__ void __launch_bounds__(kSkNT) k_skel_a(Prob P, EngineGlobals* G) {
                 if (b < nb) {
                     int lx, ly;
                     bcell(b, g.ex, g.ey, lx, ly);
-                    const int c = ly * SX + lx, r = (ly + 1) * SRX + lx + 1;
+                    const int r = (ly + 1) * SRX + lx + 1;
                     if (S.cg[r] & kGlob) {
-                        for (int k = 0; k < 8; ++k) {
-                            const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
-                            nd += (cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) &&
-                                  !in_ext(lx + offx(k), ly + offy(k), g);
-                        }
-                        const uint16_t p = S.qp[c];
-                        if (nd && (p & kPtrFinal) && (p & kPtrExit)) {
+                        nd = S.bnd[b];
+                        const uint16_t p = S.broot[b];
+                        if (nd && (p & kPtrExit)) {
                             const int xc = p & 0xFFF;
                             x = bindex(xc - (xc / SX) * SX, xc / SX, g.ex, g.ey);
                         }
@@ -429,35 +603,34 @@ __global__ void __launch_bounds__(kSkNT) k_skel_a(Prob P, EngineGlobals* G) {
             const int c = ly * SX + lx, r = (ly + 1) * SRX + lx + 1;
             if (!(S.cg[r] & kGlob)) continue;
             const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
-            const uint16_t p = S.qp[c];
+            const uint16_t p = S.broot[b];
             const bool exit = (p & kPtrExit) && (p & 0xFFF) == c;
-            int nd = 0;
-            for (int k = 0; k < 8; ++k) {
-                const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
-                nd += (cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && !in_ext(lx + offx(k), ly + offy(k), g);
-            }
+            const int nd = S.bnd[b];
             if (exit) {
-                const unsigned long long len = S.bslots[b];
-                const bool fin = (S.pk[c] & kFin) != 0;
+                const unsigned long long len = kPush ? (unsigned long long)S.bdep[b] : S.bslots[b];
+                bool fin;
+                if constexpr (kPush) fin = (S.pw[c] >> 56) == kDone;
+                else fin = (S.pk[c] & kFin) != 0;
                 const unsigned long long pend = fin ? len : kLkNever;
-                P.link[gi] = (int64_t)(kLkExit | pend | ((unsigned long long)S.bbeg[b] << 16) | (len << 32));
+                const unsigned long long beg = kPush ? 0ull : S.bbeg[b];
+                P.link[gi] = (int64_t)(kLkExit | pend | (beg << 16) | (len << 32));
                 if (fin && len == 0) {
                     const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
                     P.skstarts[slot] = (unsigned long long)gi;
                 }
             } else if (nd) {
-                const bool to_exit = (p & kPtrFinal) && (p & kPtrExit);
                 unsigned long long rec = 0;
-                if (to_exit) {
+                if (p & kPtrExit) {
                     const int xc = p & 0xFFF;
                     rec = kLkEntry | (unsigned long long)((g.y0 + xc / SX) * P.nx + g.x0 + (xc - (xc / SX) * SX));
                 }
                 P.link[gi] = (int64_t)rec;
             }
-            if (nd && (p & kPtrFinal) && (p & kPtrExit)) {
+            if (!kPush && nd && (p & kPtrExit)) {
                 const int xc = p & 0xFFF;
                 const int xb = bindex(xc - (xc / SX) * SX, xc / SX, g.ex, g.ey);
                 int s = S.bbeg[xb] + S.brank[b];
+#pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int j = r + offy(k) * SRX + offx(k);
                     const uint8_t cj = S.cg[j];
@@ -467,16 +640,19 @@ __global__ void __launch_bounds__(kSkNT) k_skel_a(Prob P, EngineGlobals* G) {
             }
         }
         // ---- in-tile partial values of the finished global cells
-        for (int c = tid; c < SN; c += kSkNT) {
+        for (int i = tid; i < ng; i += kSkNT) {
+            const int c = S.gl[i];
             const int ly = c / SX, lx = c - ly * SX;
-            if (lx >= g.ex || ly >= g.ey) continue;
-            if (!(S.cg[(ly + 1) * SRX + lx + 1] & kGlob) || !(S.pk[c] & kFin)) continue;
             const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
-            if constexpr (W) {
+            if constexpr (kPush) {
+                const unsigned long long w = S.pw[c];
+                if ((w >> 56) == kDone) wr_area(P, gi, w & kPwVal);
+            } else {
+                if (!(S.pk[c] & kFin)) continue;
                 wr_f(P.out_hi, P, gi, S.hi[c], 33);
                 wr_f(P.out_lo, P, gi, S.lo[c], 34);
+                if constexpr (AREA) wr_area(P, gi, S.ar[c]);
             }
-            if constexpr (AREA) wr_area(P, gi, S.ar[c]);
         }
     }
 }
@@ -491,6 +667,32 @@ __global__ void __launch_bounds__(256) k_skel_walk(Prob P, EngineGlobals* G) {
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         int64_t x = (int64_t)__ldcg(P.skstarts + i);
+        if constexpr (AREA && !W) {
+            // areas alone: every dependency adds its total into the exit's
+            // area (exact integer atomics, any order), so the arrival that
+            // completes the count finds the exit's total there
+            for (;;) {
+                const uint8_t k = rd_rb(P, x);
+                const unsigned long long a = rd_area(P, x);
+                if (FR_OK(x, ncell(P), 41)) done[x] = 1;
+                if (k >= 8) break;
+                const int64_t s = x + offi(k, P.nx);
+                const unsigned long long rs = (unsigned long long)__ldcg(
+                    reinterpret_cast<const unsigned long long*>(P.link) + s);
+                int64_t q;
+                if ((rs & kLkKind) == kLkExit) q = s;
+                else if ((rs & kLkKind) == kLkEntry) q = (int64_t)(rs & kLkCell);
+                else break;
+                if (!FR_OK(q, ncell(P), 42)) break;
+                atomicAdd(reinterpret_cast<unsigned long long*>(P.area) + q, a);
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> at(
+                    reinterpret_cast<unsigned long long*>(P.link)[q]);
+                const unsigned long long old = at.fetch_sub(1ull, cuda::memory_order_acq_rel);
+                if ((old & 0xFFFFull) != 1ull) break;
+                x = q;
+            }
+            continue;
+        }
         for (;;) {
             const uint8_t k = rd_rb(P, x);
             const unsigned long long rec = (unsigned long long)__ldcg(
@@ -541,9 +743,10 @@ __global__ void __launch_bounds__(256) k_skel_walk(Prob P, EngineGlobals* G) {
 // Pass C: inflows of the entries passed down the in-tile receivers; final
 // values of the global cells; completion count.
 template <bool W, bool AREA>
-__global__ void __launch_bounds__(kSkNT) k_skel_fix(Prob P, EngineGlobals* G,
+__global__ void __launch_bounds__(kSkNT, 3) k_skel_fix(Prob P, EngineGlobals* G,
                                                    unsigned long long total_cells) {
     using Sm = SmemSk<W, AREA>;
+    constexpr bool kPush = Sm::kPush;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm& S = *reinterpret_cast<Sm*>(smem_raw);
     if (__ldcg(&G->glist_count) < P.skel_min) return;
@@ -559,68 +762,162 @@ __global__ void __launch_bounds__(kSkNT) k_skel_fix(Prob P, EngineGlobals* G,
             S.qtail = 0;
             S.head = 0;
         }
-        load_ring(S, P, g);
-        for (int c0 = 0; c0 < SN; c0 += kSkNT) {
-            const int c = c0 + tid;
-            int start = -1;
-            const int ly = c / SX, lx = c - ly * SX;
+        load_tile(S, P, g);
+        const int ng = S.ng;
+        // ---- inflow of every entry: the totals of its donors in other tiles
+        // (exits, final after pass B), one thread per boundary cell
+        const int nb = nboundary(g.ex, g.ey);
+        for (int b = tid; b < nb; b += kSkNT) {
+            int lx, ly;
+            bcell(b, g.ex, g.ey, lx, ly);
             const int r = (ly + 1) * SRX + lx + 1;
-            if (lx < g.ex && ly < g.ey && (S.cg[r] & kGlob)) {
+            if (!(S.cg[r] & kGlob)) continue;
+            const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
+            uint32_t ext = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
+                if ((cj & kGlob) && (cj & 15u) == (uint8_t)opp(k) && !in_ext(lx + offx(k), ly + offy(k), g))
+                    ext |= 1u << k;
+            }
+            float h[8], l[8];
+            unsigned long long av[8];
+            uint8_t dn[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int64_t gj = gi + offi(k, P.nx);
+                h[k] = l[k] = 0.0f;
+                av[k] = 0;
+                dn[k] = 1;
+                if ((ext >> k) & 1u) {
+                    dn[k] = done_b[gj];
+                    if constexpr (W) {
+                        h[k] = rd_cg(P.out_hi, P, gj, 43);
+                        l[k] = rd_cg(P.out_lo, P, gj, 44);
+                    }
+                    if constexpr (AREA) av[k] = rd_area(P, gj);
+                }
+            }
+            df v = df_make(0.0f);
+            unsigned long long a = 0;
+            uint32_t fl = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (!((ext >> k) & 1u)) continue;
+                fl |= kUp;
+                if (!dn[k]) fl |= kPoison;
+                if constexpr (W) v = df_add(v, df{h[k], l[k]});
+                a += av[k];
+            }
+            S.bval[b] = a;
+            S.bfl[b] = fl;
+            if constexpr (W) {
+                S.bhi[b] = v.hi;
+                S.blo[b] = v.lo;
+            }
+        }
+        __syncthreads();
+        for (int i0 = 0; i0 < ng; i0 += kSkNT) {  // warp-uniform trip count
+            const int i = i0 + tid;
+            int start = -1;
+            if (i < ng) {
+                const int c = S.gl[i];
+                const int ly = c / SX, lx = c - ly * SX;
+                const int r = (ly + 1) * SRX + lx + 1;
                 const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
-                df v = df_make(0.0f);
-                unsigned long long a = 0;
-                uint32_t nin = 0, fl = 0;
-#pragma unroll 1
+                uint32_t ext = 0, din = 0, fl = 0;
+#pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint8_t cj = S.cg[r + offy(k) * SRX + offx(k)];
                     if (!(cj & kGlob) || (cj & 15u) != (uint8_t)opp(k)) continue;
-                    if (in_ext(lx + offx(k), ly + offy(k), g)) {
-                        ++nin;
-                        continue;
-                    }
-                    // a donor in another tile: an exit, final after pass B
-                    const int64_t gj = gi + offi(k, P.nx);
-                    fl |= kUp;
-                    if (!done_b[gj]) fl |= kPoison;
-                    if constexpr (W) v = df_add(v, df{rd_cg(P.out_hi, P, gj, 43), rd_cg(P.out_lo, P, gj, 44)});
-                    if constexpr (AREA) a += rd_area(P, gj);
+                    if (in_ext(lx + offx(k), ly + offy(k), g)) din |= 1u << k;
+                    else ext |= 1u << k;  // a donor in another tile: an exit, final after pass B
                 }
-                if constexpr (W) {
+                df v = df_make(0.0f);
+                unsigned long long a = 0;
+                if (ext) {  // an entry (on the boundary): its inflow from the pass above
+                    const int b = bindex(lx, ly, g.ex, g.ey);
+                    fl = S.bfl[b];
+                    a = S.bval[b];
+                    if constexpr (W) v = df{S.bhi[b], S.blo[b]};
+                }
+                const uint32_t nin = __popc(din);
+                S.nin[c] = (uint8_t)nin;
+                S.sc[c] = succ_word(S.cg, c, r, g);
+                if constexpr (kPush) {
+                    S.pw[c] = (unsigned long long)(kDone - nin) << 56 | ((fl & kPoison) ? kPwPois : 0ull) | a;
+                } else {
                     S.hi[c] = v.hi;
                     S.lo[c] = v.lo;
+                    if constexpr (AREA) S.ar[c] = a;
+                    S.pk[c] = nin | fl;
+                    S.dm[c] = (uint8_t)din;
                 }
-                if constexpr (AREA) S.ar[c] = a;
-                S.pk[c] = nin | fl;
                 if (nin == 0) start = c;
             }
             push_start(S, start);
         }
         __syncthreads();
-        tile_walk<W, AREA>(S, g);
+        if constexpr (kPush) walk_push(S);
+        else walk_pull<AREA>(S);
         __syncthreads();
-        for (int c = tid; c < SN; c += kSkNT) {
-            const int ly = c / SX, lx = c - ly * SX;
-            const int r = (ly + 1) * SRX + lx + 1;
-            if (lx >= g.ex || ly >= g.ey || !(S.cg[r] & kGlob)) continue;
-            const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
-            const int k = S.cg[r] & 15;
-            const bool exit = k < 8 && (S.cg[r + offy(k) * SRX + offx(k)] & kGlob) &&
-                              !in_ext(lx + offx(k), ly + offy(k), g);
-            if (exit) {
-                done += done_b[gi] ? 1 : 0;
-                continue;
+        // final values: L (pass A, in the outputs) plus the inflow sums, in
+        // batches of eight cells per thread whose loads are issued together
+        constexpr int B = 8;
+        for (int i0 = 0; i0 < ng; i0 += B * kSkNT) {
+            int64_t gix[B];
+            bool upd[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int i = i0 + q * kSkNT + tid;
+                upd[q] = false;
+                gix[q] = 0;
+                if (i >= ng) continue;
+                const int c = S.gl[i];
+                const int ly = c / SX, lx = c - ly * SX;
+                gix[q] = (g.y0 + ly) * P.nx + g.x0 + lx;
+                if (S.sc[c] & kPtrExit) {  // an exit: final after pass B
+                    done += done_b[gix[q]] ? 1 : 0;
+                    continue;
+                }
+                if constexpr (kPush) {
+                    const unsigned long long w = S.pw[c];
+                    if ((w >> 56) != kDone || ((w >> 48) & 0xFFull)) continue;
+                    ++done;
+                    upd[q] = (w & kPwVal) != 0;  // inflow from other tiles
+                } else {
+                    const uint32_t pkc = S.pk[c];
+                    if (!(pkc & kFin) || (pkc & kPoison)) continue;
+                    ++done;
+                    upd[q] = (pkc & kUp) != 0;  // else L is final
+                }
             }
-            const uint32_t pkc = S.pk[c];
-            if (!(pkc & kFin) || (pkc & kPoison)) continue;
-            ++done;
-            if (!(pkc & kUp)) continue;  // no inflow from other tiles: L is final
-            if constexpr (W) {
-                const df v = df_add(df{rd_cg(P.out_hi, P, gi, 45), rd_cg(P.out_lo, P, gi, 46)},
-                                    df{S.hi[c], S.lo[c]});
-                wr_f(P.out_hi, P, gi, v.hi, 47);
-                wr_f(P.out_lo, P, gi, v.lo, 48);
+            float hh[B], ll[B];
+            unsigned long long aa[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                hh[q] = ll[q] = 0.0f;
+                aa[q] = 0;
+                if (!upd[q]) continue;
+                if constexpr (W) {
+                    hh[q] = rd_cg(P.out_hi, P, gix[q], 45);
+                    ll[q] = rd_cg(P.out_lo, P, gix[q], 46);
+                }
+                if constexpr (AREA) aa[q] = rd_area(P, gix[q]);
             }
-            if constexpr (AREA) wr_area(P, gi, rd_area(P, gi) + S.ar[c]);
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                if (!upd[q]) continue;
+                const int c = S.gl[i0 + q * kSkNT + tid];
+                if constexpr (kPush) {
+                    wr_area(P, gix[q], aa[q] + (S.pw[c] & kPwVal));
+                } else {
+                    const df v = df_add(df{hh[q], ll[q]}, df{S.hi[c], S.lo[c]});
+                    wr_f(P.out_hi, P, gix[q], v.hi, 47);
+                    wr_f(P.out_lo, P, gix[q], v.lo, 48);
+                    if constexpr (AREA) wr_area(P, gix[q], aa[q] + S.ar[c]);
+                }
+            }
         }
     }
     // completion count; the last CTA checks that every cell was computed
