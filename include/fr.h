@@ -283,6 +283,11 @@ fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint3
  *   the caller's stream at the start of each call.  Calls whose GPU work
  *   overlaps (different streams, or different host threads on one device)
  *   race on the array and give wrong results; serialise them.
+ *   Device-side errors (a cycle in the routing) are not reported: the status
+ *   word lives in the array, which fr_get_status cannot address.  Argument
+ *   errors are returned as usual.
+ *   The array's address is looked up once per device and kept: do not call
+ *   this after a device reset (cudaDeviceReset) in the same process.
  */
 #define FR_NOALLOC_MAX_CELLS ((int64_t)1 << 20)
 fr_status fr_route_d8_noalloc(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
@@ -346,7 +351,8 @@ typedef struct {
  * Batched routing of many independent DEMs of uneven size (receivers +
  * accumulation for every tile) with one launch per stage over all tiles,
  * persistent CTAs taking work from device-side counters; the sequence reads
- * no host memory when it executes and can be captured in a CUDA graph.  All
+ * no host memory when it executes and can be captured in a CUDA graph.
+ * At most 2^24 - 1 tiles per call.  All
  * tiles must request the same outputs (w_out / area_out set for all or none;
  * area_out only with FR_ROUTING_D8, w_out required with FR_ROUTING_MFD).
  * flags: FR_EDGE_ROUTE; with FR_ROUTING_D8 also FR_D8_LOWEST and FR_D4; with
@@ -374,6 +380,28 @@ size_t fr_batch_workspace_size(const fr_tile* tiles_host, int32_t ntiles, int32_
 fr_status fr_batch_autotune(const fr_tile* tiles_host, const fr_tile* tiles_dev, int32_t ntiles,
                             int32_t kind, double p, uint32_t flags, void* ws, size_t ws_bytes,
                             void* stream);
+
+/*
+ * Receiver indices from D8 codes: out[i] = linear index (y*nx + x) of cell
+ * i's receiver, or -1 where cell i is a sink (or its code points out of the
+ * grid).  The receiver array r(i) of Sec. 2.1 in index form, for callers that
+ * work with indices rather than the direction bytes of fr_receivers_d8.
+ *   dir          [ny*nx] uint8 codes (fr_receivers_d8).
+ *   index_bytes  4 (int32; requires nx*ny <= INT32_MAX) or 8 (int64).
+ *   idx_out      [ny*nx] int32 or int64.
+ * Needs no workspace.
+ */
+fr_status fr_receiver_index(const uint8_t* dir, int64_t nx, int64_t ny, int32_t index_bytes,
+                            void* idx_out, void* stream);
+
+/*
+ * Time limit of device-side waits (the grid barrier between the rounds of the
+ * MFD and adjoint global phases), in nanoseconds of the GPU's global timer; a
+ * wait that runs out leaves FR_ERR_NO_PROGRESS in the status word and the
+ * kernel returns.  Applies to calls enqueued after it, in every thread of the
+ * process.  Default 10 s.  Returns the previous limit.
+ */
+uint64_t fr_set_wait_limit(uint64_t ns);
 
 /* Workspace bytes an operation needs for an nx-by-ny grid (0 if the sizes
  * are invalid).  FR_OP_RECEIVERS needs none. */

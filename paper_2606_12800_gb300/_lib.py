@@ -55,6 +55,7 @@ EXPORTS = (
     "fr_route_adjoint", "fr_mass_balance", "fr_route_batch", "fr_batch_workspace_size",
     "fr_batch_autotune", "fr_route_d8_noalloc", "fr_accumulate_richardson", "fr_fill",
     "fr_workspace_size", "fr_get_status", "fr_status_string", "fr_version",
+    "fr_receiver_index", "fr_set_wait_limit",
 )
 
 
@@ -122,6 +123,8 @@ def load(build_if_missing: bool = True):
             "fr_get_status": (S, [P, ctypes.c_size_t, P]),
             "fr_status_string": (ctypes.c_char_p, [S]),
             "fr_version": (I32, []),
+            "fr_receiver_index": (S, [P, I64, I64, I32, P, P]),
+            "fr_set_wait_limit": (ctypes.c_uint64, [ctypes.c_uint64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -16,7 +16,8 @@ from . import _lib
 from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_FILL, FR_OP_MFD, FR_OP_ROUTE, check,
                    fr_routing, load)
 
-_ws_cache: Dict[int, torch.Tensor] = {}
+# one workspace per (device, stream): calls on different streams may overlap
+_ws_cache: Dict[tuple, torch.Tensor] = {}
 
 
 def _stream() -> ctypes.c_void_p:
@@ -46,10 +47,11 @@ def workspace(nx: int, ny: int, device=None, mfd: bool = False) -> torch.Tensor:
     need = int(load().fr_workspace_size(FR_OP_MFD if mfd else FR_OP_ROUTE, nx, ny, 0))
     if need == 0:
         raise ValueError("invalid grid size %dx%d" % (nx, ny))
-    ws = _ws_cache.get(idx)
+    key = (idx, torch.cuda.current_stream(torch.device("cuda", idx)).cuda_stream)
+    ws = _ws_cache.get(key)
     if ws is None or ws.numel() < need:
         ws = torch.empty(need, dtype=torch.uint8, device=torch.device("cuda", idx))
-        _ws_cache[idx] = ws
+        _ws_cache[key] = ws
     return ws
 
 
@@ -256,10 +258,27 @@ def get_status(device=None) -> int:
     status word of the cached workspace (0 = ok)."""
     dev = torch.device(device if device is not None else "cuda")
     idx = dev.index if dev.index is not None else torch.cuda.current_device()
-    ws = _ws_cache.get(idx)
+    ws = _ws_cache.get((idx, torch.cuda.current_stream(torch.device("cuda", idx)).cuda_stream))
     if ws is None:
         return 0
     return int(load().fr_get_status(_p(ws), ws.numel(), _stream()))
+
+
+def receiver_index(dir_: torch.Tensor, wide: bool = True) -> torch.Tensor:
+    """Linear receiver index of every cell (-1 for sinks) from D8 codes
+    (fr_receiver_index); int64, or int32 with wide=False."""
+    _check_grid(dir_, torch.uint8, "dir")
+    ny, nx = dir_.shape
+    out = torch.empty((ny, nx), dtype=torch.int64 if wide else torch.int32, device=dir_.device)
+    check(load().fr_receiver_index(_p(dir_), nx, ny, 8 if wide else 4, _p(out), _stream()),
+          "fr_receiver_index")
+    return out
+
+
+def set_wait_limit(ns: int) -> int:
+    """Limit of device-side waits in nanoseconds (fr_set_wait_limit); returns
+    the previous limit."""
+    return int(load().fr_set_wait_limit(int(ns)))
 
 
 class RouteMFD(torch.autograd.Function):
@@ -279,9 +298,13 @@ class RouteMFD(torch.autograd.Function):
     def backward(ctx, grad_w):
         dem, mask, w, w_lo = ctx.saved_tensors
         dx, p, flags = ctx.cfg
+        want_dz = ctx.needs_input_grad[0]
+        want_dr = ctx.needs_input_grad[1]
+        if not (want_dz or want_dr):
+            return None, None, None, None, None
         R = routing_mfd(mask, dem, dx, p, flags)
-        dLdr, dLdz = adjoint(R, w, w_lo, dLdw=grad_w.contiguous().float(), want_dz=True)
-        return dLdz, dLdr, None, None, None
+        dLdr, dLdz = adjoint(R, w, w_lo, dLdw=grad_w.contiguous().float(), want_dz=want_dz)
+        return (dLdz if want_dz else None), (dLdr if want_dr else None), None, None, None
 
 
 def route_batch(dems, rains=None, kind: str = "d8", dx: float = 30.0, p: float = 1.1,

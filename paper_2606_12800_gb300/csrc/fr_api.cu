@@ -1,5 +1,7 @@
 // fr_api.cu -- the C ABI declared in include/fr.h: argument validation,
 // workspace layout, status word and the launch sequences.
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -152,12 +154,29 @@ Prob base_prob(const fr_routing* R, char* ws) {
     return P;
 }
 
+std::atomic<unsigned long long> g_wait_limit_ns{10ull * 1000ull * 1000ull * 1000ull};
+
 }  // namespace
+
+unsigned long long wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+
 }  // namespace fr
 
 using namespace fr;
 
 extern "C" {
+
+uint64_t fr_set_wait_limit(uint64_t ns) {
+    return g_wait_limit_ns.exchange(ns, std::memory_order_relaxed);
+}
+
+fr_status fr_receiver_index(const uint8_t* dir, int64_t nx, int64_t ny, int32_t index_bytes,
+                            void* idx_out, void* stream) {
+    if (!dir || !idx_out || !sizes_ok(nx, ny) || (index_bytes != 4 && index_bytes != 8))
+        return FR_ERR_INVALID_ARG;
+    if (index_bytes == 4 && nx * ny > (int64_t)INT32_MAX) return FR_ERR_INVALID_ARG;
+    return cuda_status(launch_receiver_index(dir, nx, ny, index_bytes == 8, idx_out, (cudaStream_t)stream));
+}
 
 const char* fr_status_string(fr_status s) {
     switch (s) {

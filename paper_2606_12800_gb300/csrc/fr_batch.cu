@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(SETUP_NT) k_batch_setup(const fr_tile* __restr
 }
 
 bool tiles_ok(const fr_tile* t, int n, int kind) {
-    if (!t || n <= 0) return false;
+    // global-cell list entries keep the problem index in 24 bits
+    if (!t || n <= 0 || n >= (1 << 24)) return false;
     const bool w = t[0].w_out != nullptr, a = t[0].area_out != nullptr;
     if (!w && !a) return false;
     if (kind == FR_ROUTING_MFD && (a || !w)) return false;

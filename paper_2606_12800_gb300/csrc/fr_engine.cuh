@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(256) k_global(const Prob* __restrict__ probs, 
 // (cooperative launch, so all blocks are resident); the barrier's wait is
 // bounded in time.
 
-constexpr unsigned long long kBarrierLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
+// The barrier's wait limit is a kernel argument: the library-wide value set
+// by fr_set_wait_limit (default 10 s).
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -400,8 +401,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 // Barrier over all blocks of a cooperative launch.  Returns false (and leaves
-// FR_ERR_NO_PROGRESS in the status word) if the wait exceeds the time limit.
-static __device__ __noinline__ bool grid_barrier(EngineGlobals* G, unsigned nblocks) {
+// FR_ERR_NO_PROGRESS in the status word) if the wait exceeds limit_ns.
+static __device__ __noinline__ bool grid_barrier(EngineGlobals* G, unsigned nblocks,
+                                                 unsigned long long limit_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -417,7 +419,7 @@ static __device__ __noinline__ bool grid_barrier(EngineGlobals* G, unsigned nblo
             const unsigned long long t0 = global_ns();
             while (ld_acquire_u32(&G->bar_gen) == gen) {
                 __nanosleep(64);
-                if (global_ns() - t0 > kBarrierLimitNs) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicMax(&G->status, kStatusNoProgress);
                     ok = 0;
                     break;
@@ -461,7 +463,8 @@ __device__ __noinline__ void step_round(const Prob& P, int64_t cur, unsigned lon
 template <Mode M, bool W, bool AREA>
 __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ probs, Prob single,
                                                        EngineGlobals* G,
-                                                       unsigned long long total_cells) {
+                                                       unsigned long long total_cells,
+                                                       unsigned long long limit_ns) {
     using E = Eng<M, W, AREA>;
     __shared__ unsigned long long s_done;
     const Prob& P0 = probs ? probs[0] : single;
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
         const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
         if (FR_OK((int64_t)slot, (int64_t)cap, 18)) buf_a[slot] = item;
     }
-    if (ok) ok = grid_barrier(G, nb);
+    if (ok) ok = grid_barrier(G, nb, limit_ns);
     for (int round = 1; ok; ++round) {
         unsigned long long* cur = (round & 1) ? buf_a : buf_b;
         unsigned long long* nxt = (round & 1) ? buf_b : buf_a;
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
             step_round<E>(P, (int64_t)(item & kCellMask), item & ~kCellMask, nxt, ncount, cap);
             ++done;
         }
-        ok = grid_barrier(G, nb);
+        ok = grid_barrier(G, nb, limit_ns);
     }
     for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
     if (threadIdx.x == 0) s_done = 0;
@@ -560,7 +563,8 @@ cudaError_t launch_global(const Prob* probs, const Prob& single, EngineGlobals* 
         Prob one = single;
         const Prob* pp = probs;
         unsigned long long total = total_cells;
-        void* args[] = {(void*)&pp, (void*)&one, (void*)&G, (void*)&total};
+        unsigned long long limit = wait_limit_ns();
+        void* args[] = {(void*)&pp, (void*)&one, (void*)&G, (void*)&total, (void*)&limit};
         return cudaLaunchCooperativeKernel((const void*)k_global_levels<M, W, AREA>, dim3(grid),
                                            dim3(256), args, 0, s);
     }

@@ -73,6 +73,12 @@ enum class Mode : int { FwdD8 = 0, FwdMfd = 1, AdjD8 = 2, AdjMfd = 3 };
 
 // Grid of the D8 forward walker kernel (fr_accumulate.cu).
 int walker_grid();
+// Time a device-side wait may take before the call reports
+// FR_ERR_NO_PROGRESS (fr_set_wait_limit; fr_api.cu).
+unsigned long long wait_limit_ns();
+// Linear receiver index of every cell from D8 codes (fr_receivers.cu).
+cudaError_t launch_receiver_index(const uint8_t* dir, int64_t nx, int64_t ny, bool wide, void* out,
+                                  cudaStream_t s);
 // Skeleton tiles of the D8 global phase (fr_skel.cu): kSkelTile x kSkelTile
 // cells; kSkelPool dependency slots per tile (a dependency is a donor in the
 // one-cell ring around the tile, and each ring cell has one receiver).

@@ -321,7 +321,37 @@ __global__ void k_count_nonfinite(const float* __restrict__ z, int64_t n,
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
 }
 
+// Linear index of each cell's receiver (-1 for sinks and for codes that
+// point out of the grid), four cells per thread step.
+template <class I>
+__global__ void __launch_bounds__(256) k_receiver_index(const uint8_t* __restrict__ dir, int64_t nx,
+                                                        int64_t n, I* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t k = __ldg(dir + i);
+        I r = (I)-1;
+        if (k < 8) {
+            const int64_t y = i / nx, x = i - y * nx;
+            const int64_t xr = x + offx((int)k), yr = y + offy((int)k);
+            if (xr >= 0 && yr >= 0 && xr < nx && yr * nx + xr < n) r = (I)(yr * nx + xr);
+        }
+        out[i] = r;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_receiver_index(const uint8_t* dir, int64_t nx, int64_t ny, bool wide, void* out,
+                                  cudaStream_t s) {
+    const int64_t n = nx * ny;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (wide)
+        k_receiver_index<int64_t><<<(unsigned)blocks, 256, 0, s>>>(dir, nx, n, (int64_t*)out);
+    else
+        k_receiver_index<int32_t><<<(unsigned)blocks, 256, 0, s>>>(dir, nx, n, (int32_t*)out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_receivers_d8(const float* z, int64_t nx, int64_t ny, double dx,
                                 uint32_t flags, uint8_t* dir, uint8_t* indeg, cudaStream_t s) {

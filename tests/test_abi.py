@@ -105,3 +105,30 @@ def test_argument_validation_is_synchronous(lib):
     assert lib.fr_route_adjoint(ctypes.byref(R), fake, None, None, fake, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
     R.reserved = 1
     assert lib.fr_mass_balance(ctypes.byref(R), None, fake, None, None, fake, fake, 1 << 20, None) == _lib.FR_ERR_INVALID_ARG
+
+
+def test_receiver_index_and_wait_limit_validation(lib):
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    assert lib.fr_receiver_index(None, 4, 4, 8, fake, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receiver_index(fake, 4, 4, 8, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receiver_index(fake, 4, 4, 2, fake, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receiver_index(fake, 0, 4, 4, fake, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receiver_index(fake, 1 << 16, 1 << 16, 4, fake, None) == _lib.FR_ERR_INVALID_ARG
+    prev = lib.fr_set_wait_limit(123)
+    assert lib.fr_set_wait_limit(prev) == 123
+
+
+def test_batch_and_global_phase_flags_validation(lib):
+    P = ctypes.c_void_p
+    tiles = (_lib.fr_tile * 1)()
+    t = tiles[0]
+    t.dem, t.route_out, t.w_out, t.nx, t.ny, t.dx = 0x1000, 0x2000, 0x3000, 8, 8, 30.0
+    assert lib.fr_batch_workspace_size(tiles, 1, _lib.FR_ROUTING_D8, 0) > 0
+    assert lib.fr_batch_workspace_size(tiles, 1 << 24, _lib.FR_ROUTING_D8, 0) == 0
+    R = _lib.fr_routing()
+    R.kind, R.nx, R.ny, R.dir = _lib.FR_ROUTING_D8, 8, 8, 0x1000
+    R.flags = _lib.FR_GLOBAL_WALKERS | _lib.FR_GLOBAL_SKELETON
+    fake = P(0x1000)
+    assert lib.fr_accumulate(ctypes.byref(R), None, None, None, fake, fake, 1 << 20, None) == \
+        _lib.FR_ERR_INVALID_ARG

@@ -1,8 +1,9 @@
 """fr_route_d8_noalloc: the D8 route on the library's own fixed device scratch.
 
 The entry point serves callers that cannot allocate device memory.  It must
-return exactly what fr_route_d8 (caller workspace) returns, on consecutive
-calls that share the scratch, and reject grids above its limit.  This file is
+return exactly what fr_route_d8 (caller workspace) returns, and what the CPU
+oracle computes, on consecutive calls that share the scratch, and reject grids
+above its limit.  This file is
 collected last so that it also runs after every other test in one process.
 """
 import ctypes
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2606_12800_gb300 import _lib, inputs
 
 RTOL_W = 1e-6
@@ -77,3 +79,11 @@ def test_noalloc_matches_route_d8_on_consecutive_calls():
         np.testing.assert_allclose(full1, full0, rtol=RTOL_W, atol=0)
         np.testing.assert_allclose(w1, w0, rtol=RTOL_W, atol=0)
         assert np.isfinite(w1).all() and (a1 >= 1).all()
+        # and directly against the oracle (FP64 water, uint64 areas)
+        zn = z.cpu().numpy()
+        rn = rain.cpu().numpy() if rain is not None else None
+        d_ref, w_ref, _, order = oracle.route_d8(zn, dx, rn, flags)
+        _, a_ref = oracle.accumulate_d8(d_ref, order, None)
+        np.testing.assert_array_equal(d1, d_ref)
+        np.testing.assert_array_equal(a1.astype(np.uint64), a_ref)
+        assert np.max(np.abs(w1.astype(np.float64) - w_ref) / w_ref) <= RTOL_W
