@@ -215,6 +215,9 @@ fr_status fr_get_status(const void* ws, size_t ws_bytes, void* stream) {
         cudaSuccess)
         return FR_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FR_ERR_CUDA;
+    unsigned tma_err = 0;
+    if (read_clear_tma_error(&tma_err, s) != cudaSuccess) return FR_ERR_CUDA;
+    if (g.status == FR_OK && tma_err) return FR_ERR_NO_PROGRESS;
     return (fr_status)g.status;
 }
 

@@ -76,6 +76,9 @@ int walker_grid();
 // Time a device-side wait may take before the call reports
 // FR_ERR_NO_PROGRESS (fr_set_wait_limit; fr_api.cu).
 unsigned long long wait_limit_ns();
+// Reads and clears the flag a TMA wait that ran out leaves (fr_receivers.cu);
+// synchronises the stream.
+cudaError_t read_clear_tma_error(unsigned* out, cudaStream_t s);
 // Linear receiver index of every cell from D8 codes (fr_receivers.cu).
 cudaError_t launch_receiver_index(const uint8_t* dir, int64_t nx, int64_t ny, bool wide, void* out,
                                   cudaStream_t s);

@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "fr_internal.h"
+#include "fr_tma.cuh"
 
 namespace fr {
 
@@ -156,6 +157,137 @@ __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ 
     int64_t x0, y0;
     tile_origin(nx, x0, y0);
     recv_d8_tile<INDEG, LOWEST>(z, nx, ny, c_orth, c_diag, flags, dir, indeg, x0, y0);
+}
+
+// ---------------------------------------------------------------- TMA path
+// D8 codes without donor counts, by a persistent kernel: each CTA walks its
+// tiles of TTX x TTY cells, the elevations of a tile plus a one-cell halo
+// arriving by TMA into one of NS shared-memory stages while the previous tiles
+// are computed.  The box starts 4 cells left of the tile (its x coordinate a
+// multiple of 4, as TMA requires), so it is TTX + 8 wide.
+constexpr int TTX = 128, TTY = 32, TNS = 3;
+constexpr int TBX = TTX + 8, TBY = TTY + 2;
+constexpr unsigned kTileBytes = TBX * TBY * 4;
+static_assert((TBX * 4) % 16 == 0, "TMA box rows are whole 16-byte units");
+
+// Set when a TMA wait ran out (read and cleared by fr_get_status).
+__device__ unsigned g_tma_wait_error;
+
+struct alignas(128) TmaStage {  // TMA writes whole boxes to 128-byte aligned addresses
+    float v[TBY * TBX];
+};
+struct TmaSmem {
+    TmaStage buf[TNS];
+    alignas(8) uint64_t bar[TNS];
+};
+
+template <bool LOWEST, bool D4>
+__global__ void __launch_bounds__(256) k_receivers_d8_tma(const __grid_constant__ CUtensorMap zmap,
+                                                          int64_t nx, int64_t ny, float c_orth,
+                                                          float c_diag, uint32_t flags,
+                                                          uint8_t* __restrict__ dir, int64_t ntiles,
+                                                          int tiles_x, unsigned long long limit_ns) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaSmem& S = *reinterpret_cast<TmaSmem*>(smem_raw);
+    const bool edge_route = flags & kEdgeRoute;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < TNS; ++s) mbar_init(&S.bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t t, int s) {
+        const int64_t ty = t / tiles_x, tx = t - ty * tiles_x;
+        mbar_expect_tx(&S.bar[s], kTileBytes);
+        tma_load_2d(S.buf[s].v, &zmap, (int)(tx * TTX - 4), (int)(ty * TTY - 1), &S.bar[s]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < TNS; ++s) {
+            const int64_t t = (int64_t)blockIdx.x + (int64_t)s * gridDim.x;
+            if (t < ntiles) issue(t, s);
+        }
+    const int lane = tid & 31, warp = tid >> 5, qx = 4 * lane;
+    int i = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % TNS;
+        const bool ok = mbar_wait(&S.bar[s], (unsigned)(i / TNS) & 1u, limit_ns);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not arrive: report, let the other copies in flight
+            // land (bounded), and leave (the whole block takes this branch)
+            if (tid == 0) {
+                atomicOr(&g_tma_wait_error, 1u);
+                for (int k = 1; k < TNS; ++k) {
+                    const int64_t tk = t + (int64_t)k * gridDim.x;
+                    if (tk < ntiles) mbar_wait(&S.bar[(i + k) % TNS], (unsigned)((i + k) / TNS) & 1u, limit_ns);
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        const int64_t ty = t / tiles_x, tx = t - ty * tiles_x;
+        const int64_t x0 = tx * TTX, y0 = ty * TTY;
+        const bool interior = x0 >= 1 && y0 >= 1 && x0 + TTX + 1 <= nx && y0 + TTY + 1 <= ny;
+        const float* b = S.buf[s].v;
+        for (int r = warp; r < TTY; r += 8) {
+            // 3 x 12 window: buffer rows r .. r + 2, columns qx .. qx + 11
+            // (tile column c sits at buffer column c + 4)
+            float w[3][12];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const float4 f = *reinterpret_cast<const float4*>(b + (r + a) * TBX + qx + 4 * v);
+                    w[a][4 * v] = f.x;
+                    w[a][4 * v + 1] = f.y;
+                    w[a][4 * v + 2] = f.z;
+                    w[a][4 * v + 3] = f.w;
+                }
+            uint32_t packed = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = q + 4;  // window column of the cell
+                float zn[8];
+                zn[0] = w[1][c + 1];
+                zn[1] = w[0][c];
+                zn[2] = w[1][c - 1];
+                zn[3] = w[2][c];
+                if (D4) {
+                    zn[4] = zn[5] = zn[6] = zn[7] = __int_as_float(0x7f800000);
+                } else {
+                    zn[4] = w[0][c + 1];
+                    zn[5] = w[0][c - 1];
+                    zn[6] = w[2][c - 1];
+                    zn[7] = w[2][c + 1];
+                }
+                uint32_t code = d8_code_sel<LOWEST>(w[1][c], zn, c_orth, c_diag);
+                if (!interior) {
+                    const int64_t gx = x0 + qx + q, gy = y0 + r;
+                    if (gx >= nx || gy >= ny || (!edge_route && is_edge(gx, gy, nx, ny))) code = kSink;
+                }
+                packed |= code << (8 * q);
+            }
+            const int64_t gy = y0 + r;
+            const int64_t gx = x0 + qx;
+            if (gy < ny && gx < nx) {
+                const int64_t gi = gy * nx + gx;
+                if (gx + 3 < nx && ((uintptr_t)(dir + gi) & 3) == 0) {
+                    *reinterpret_cast<uint32_t*>(dir + gi) = packed;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (gx + q < nx) dir[gi + q] = (uint8_t)(packed >> (8 * q));
+                }
+            }
+        }
+        __syncthreads();  // every thread is done with stage s
+        if (tid == 0) {
+            const int64_t tn = t + (int64_t)TNS * gridDim.x;
+            if (tn < ntiles) {
+                fence_proxy_async_smem();
+                issue(tn, s);
+            }
+        }
+    }
 }
 
 template <bool FRAC, bool INDEG>
@@ -339,7 +471,71 @@ __global__ void __launch_bounds__(256) k_receiver_index(const uint8_t* __restric
     }
 }
 
+template <bool LOWEST, bool D4>
+cudaError_t launch_d8_tma(const CUtensorMap& map, int64_t nx, int64_t ny, float co, float cd,
+                          uint32_t flags, uint8_t* dir, cudaStream_t s) {
+    constexpr size_t sm = sizeof(TmaSmem);
+    static std::atomic<unsigned long long> set_on{0};
+    static int grid_per_sm = 0, sms = 0;
+    cudaError_t e = smem_limit_once(k_receivers_d8_tma<LOWEST, D4>, sm, set_on);
+    if (e != cudaSuccess) return e;
+    if (!grid_per_sm) {
+        int dev = 0, per = 0, n = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_receivers_d8_tma<LOWEST, D4>, 256, sm)) !=
+            cudaSuccess)
+            return e;
+        sms = n;
+        grid_per_sm = per > 0 ? per : 1;
+    }
+    const int tiles_x = (int)((nx + TTX - 1) / TTX);
+    const int64_t ntiles = (int64_t)tiles_x * ((ny + TTY - 1) / TTY);
+    int64_t grid = (int64_t)sms * grid_per_sm;
+    if (grid > ntiles) grid = ntiles;
+    k_receivers_d8_tma<LOWEST, D4><<<(unsigned)grid, 256, sm, s>>>(map, nx, ny, co, cd, flags, dir, ntiles,
+                                                                   tiles_x, wait_limit_ns());
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool encode_tile_map_f32(CUtensorMap* map, const float* base, int64_t nx, int64_t ny, int box_x,
+                         int box_y) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Encode>(p);
+        looked = true;
+    }
+    if (!fn || (nx & 3) || ((uintptr_t)base & 15) || nx > (int64_t)1 << 31 || ny > (int64_t)1 << 31) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) == CUDA_SUCCESS;
+}
+
+cudaError_t read_clear_tma_error(unsigned* out, cudaStream_t s) {
+    unsigned zero = 0;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_tma_wait_error);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(out, p, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (*out == 0) return cudaSuccess;
+    if ((e = cudaMemcpyAsync(p, &zero, sizeof(unsigned), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
 
 cudaError_t launch_receiver_index(const uint8_t* dir, int64_t nx, int64_t ny, bool wide, void* out,
                                   cudaStream_t s) {
@@ -359,6 +555,15 @@ cudaError_t launch_receivers_d8(const float* z, int64_t nx, int64_t ny, double d
     float co = (float)(1.0 / dx);
     float cd = (float)(1.0 / (std::sqrt(2.0) * dx));
     const bool lowest = flags & kD8Lowest;
+    // codes alone on a TMA-addressable grid: the pipelined persistent kernel
+    CUtensorMap map;
+    if (!indeg && nx * ny >= (int64_t)TTX * TTY && encode_tile_map_f32(&map, z, nx, ny, TBX, TBY)) {
+        const bool d4 = flags & kD4;
+        if (lowest) return d4 ? launch_d8_tma<true, true>(map, nx, ny, co, cd, flags, dir, s)
+                              : launch_d8_tma<true, false>(map, nx, ny, co, cd, flags, dir, s);
+        return d4 ? launch_d8_tma<false, true>(map, nx, ny, co, cd, flags, dir, s)
+                  : launch_d8_tma<false, false>(map, nx, ny, co, cd, flags, dir, s);
+    }
     if (indeg && lowest)
         k_receivers_d8<true, true><<<grid, RNT, 0, s>>>(z, nx, ny, co, cd, flags, dir, indeg);
     else if (indeg)
