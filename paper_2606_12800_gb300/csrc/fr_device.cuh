@@ -72,25 +72,35 @@ __device__ __forceinline__ df df_mul(df a, df b) {
 
 // Sum of eight two-float terms in a fixed pairwise order:
 // ((t0 + t1) + (t2 + t3)) + ((t4 + t5) + (t6 + t7)).  Absent terms are zero,
-// which df_add passes through exactly.  The MFD kernels sum over the eight
-// directions in this order wherever they run (eight lanes with shuffles, or
-// one thread), so a cell's value does not depend on which kernel computed it.
+// which df_add passes through exactly (the MFD normaliser S uses this order).
 __device__ __forceinline__ df df_tree8(const df (&t)[8]) {
     const df a = df_add(df_add(t[0], t[1]), df_add(t[2], t[3]));
     const df b = df_add(df_add(t[4], t[5]), df_add(t[6], t[7]));
     return df_add(a, b);
 }
 
-// The same sum across the eight lanes of an aligned group (lane & 7 = term
-// index); every lane of the group returns the total.
-__device__ __forceinline__ df df_tree8_lanes(df t) {
-    const unsigned lane = threadIdx.x & 31u;
+// own + sum over k = 0..7 of f[k] * v[k], accumulated in ascending k with
+// compensation (the Dot2 scheme of Ogita, Rump and Oishi, 2005, with two-float
+// v): each product is split exactly by an FMA, each partial sum by Knuth's
+// two-sum, and the rounding errors are summed in a second float that joins the
+// result at the end.  Terms with f = 0 and v = 0 leave both floats unchanged,
+// so absent neighbours may stay in the sum.  Every kernel that pulls a cell's
+// value from its dependencies (water forward, adjoints backward) uses this one
+// order, so a cell's value does not depend on which kernel computed it.
+__device__ __forceinline__ df df_dot8(df own, const float (&f)[8], const df (&v)[8]) {
+    float s = own.hi, c = own.lo;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        const df u = {__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
-        t = (lane & (unsigned)o) ? df_add(u, t) : df_add(t, u);
+    for (int k = 0; k < 8; ++k) {
+        const float p = __fmul_rn(f[k], v[k].hi);
+        float pe = __fmaf_rn(f[k], v[k].hi, -p);
+        pe = __fmaf_rn(f[k], v[k].lo, pe);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, pe));
     }
-    return t;
+    return df_norm(s, c);
 }
 
 // ------------------------------------------------------------ D8 predicate

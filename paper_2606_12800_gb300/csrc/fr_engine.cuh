@@ -175,17 +175,18 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
     if constexpr (E::kVal) {
         df v = init_value<E>(P, t, recv);
         if constexpr (E::kAdj) {
-            // receiver terms in the fixed pairwise order of df_tree8
-            df term[8];
+            // receiver terms in the fixed order of df_dot8
+            float f[8];
+            df vv[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                term[k] = df_make(0.0f);
+                f[k] = 0.0f;
+                vv[k] = df_make(0.0f);
                 if (!((recv >> k) & 1u)) continue;
-                const df gj = g_value<E>(P, t + offi(k, P.nx));
-                if constexpr (E::kMfd) term[k] = mfd_frac(__ldg(P.frac + t * 8 + k), gj);
-                else term[k] = gj;
+                vv[k] = g_value<E>(P, t + offi(k, P.nx));
+                f[k] = E::kMfd ? __ldg(P.frac + t * 8 + k) : 1.0f;
             }
-            v = df_add(v, df_tree8(term));
+            v = df_dot8(v, f, vv);
         } else {
             // routing bytes of the eight neighbours, loaded side by side
             const uint32_t gm = grid_mask(x, y, P.nx, P.ny);
@@ -194,16 +195,19 @@ __device__ __noinline__ void walker_compute(const Prob& P, int64_t t) {
             for (int k = 0; k < 8; ++k)
                 if ((gm >> k) & 1u) dmask |= ((g_recv<E>(P, t + offi(k, P.nx)) >> opp(k)) & 1u) << k;
             if constexpr (E::kMfd) {
-                // donor terms in the fixed pairwise order of df_tree8
-                df term[8];
+                // donor terms in the fixed order of df_dot8
+                float f[8];
+                df vv[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    term[k] = df_make(0.0f);
+                    f[k] = 0.0f;
+                    vv[k] = df_make(0.0f);
                     if (!((dmask >> k) & 1u)) continue;
                     const int64_t j = t + offi(k, P.nx);
-                    term[k] = mfd_frac(__ldg(P.frac + j * 8 + opp(k)), g_value<E>(P, j));
+                    f[k] = __ldg(P.frac + j * 8 + opp(k));
+                    vv[k] = g_value<E>(P, j);
                 }
-                v = df_add(v, df_tree8(term));
+                v = df_dot8(v, f, vv);
             } else {
 #pragma unroll 1
                 for (int k = 0; k < 8; ++k) {

@@ -12,8 +12,8 @@
 // the host stops after the first sweep that changes no value.
 //
 // A cell's eight direction terms (in-tile donors from this sweep, off-tile
-// donors from the previous iterate) are summed in the fixed pairwise order of
-// df_tree8, so the converged values are bit-identical from sweep to sweep.
+// donors from the previous iterate) are accumulated in the fixed order of
+// df_dot8, so the converged values are bit-identical from sweep to sweep.
 #include "fr_engine.cuh"
 
 namespace fr {
@@ -125,23 +125,23 @@ __global__ void __launch_bounds__(kRNT) k_richardson_sweep(Prob P, const float2*
                 const int64_t gc = (y0 + ly) * P.nx + (x0 + lx);
                 // the eight donor terms: in-tile donors from this sweep, the
                 // others from the previous iterate (R w^(l))
-                df term[8];
+                float f[8];
+                df vv[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    term[k] = df_make(0.0f);
+                    f[k] = 0.0f;
+                    vv[k] = df_make(0.0f);
                     if (!((S.rb[r + offy(k) * RX + offx(k)] >> opp(k)) & 1u)) continue;
-                    df vj;
                     if ((S.dm[c] >> k) & 1u) {
                         const int j = c + offy(k) * TX + offx(k);
-                        vj = {S.vhi[j], S.vlo[j]};
+                        vv[k] = {S.vhi[j], S.vlo[j]};
                     } else {
                         const float2 pj = prev[gc + offi(k, P.nx)];
-                        vj = {pj.x, pj.y};
+                        vv[k] = {pj.x, pj.y};
                     }
-                    if constexpr (MFD) term[k] = mfd_frac(__ldg(P.frac + (gc + offi(k, P.nx)) * 8 + opp(k)), vj);
-                    else term[k] = vj;
+                    f[k] = MFD ? __ldg(P.frac + (gc + offi(k, P.nx)) * 8 + opp(k)) : 1.0f;
                 }
-                const df v = df_add(df{S.vhi[c], S.vlo[c]}, df_tree8(term));
+                const df v = df_dot8(df{S.vhi[c], S.vlo[c]}, f, vv);
                 S.vhi[c] = v.hi;
                 S.vlo[c] = v.lo;
                 S.fin[c] = 1;
