@@ -311,6 +311,35 @@ __device__ __noinline__ unsigned long long walker_d8(const Prob& P, int64_t star
     return n;
 }
 
+// Warp-aggregated append to a frontier (all 32 lanes call): lane l appends
+// pid_bits | (cell + offset of k) for the set bits k < 8 of `bits`, and
+// pid_bits | cell for bit 8.  One atomic per warp on the frontier count.
+__device__ __forceinline__ void frontier_push(int64_t nx, int64_t cell, unsigned long long pid_bits,
+                                              uint32_t bits, unsigned long long* buf,
+                                              unsigned long long* count, unsigned long long cap) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const uint32_t n = (uint32_t)__popc(bits);
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const unsigned v = __ballot_sync(0xffffffffu, (n >> b) & 1u);
+        pre += (uint32_t)__popc(v & lt) << b;
+        tot += (uint32_t)__popc(v) << b;
+    }
+    if (tot == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 0) + pre;
+    for (uint32_t m = bits; m; m &= m - 1) {
+        const int k = __ffs(m) - 1;
+        const int64_t t = k == 8 ? cell : cell + offi(k, nx);
+        if (FR_OK((int64_t)base, (int64_t)cap, 18)) buf[base] = pid_bits | (unsigned long long)t;
+        ++base;
+    }
+}
+
 // Global phase of D8 forward routing, first launch: every global cell's
 // arrival counter is preset to kReadyAt minus its number of global donors, and
 // the cells without global donors are listed (the walkers' starts, in the
@@ -324,18 +353,24 @@ __global__ void __launch_bounds__(256) k_global_init(const Prob* __restrict__ pr
     if (count >= P0.skel_min) return;  // the skeleton solve takes the global cells
     const unsigned long long* list = P0.glist;
     unsigned long long* starts = reinterpret_cast<unsigned long long*>(P0.link);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long item = __ldcg(list + i);
-        const Prob& P = probs ? probs[(int)(item >> 40)] : single;
-        const int64_t cell = (int64_t)(item & ((1ull << 40) - 1));
-        const uint32_t deps = g_deps_global<E>(P, cell);
-        if (deps) {
-            cnt_set(P, cell, kReadyAt - deps);
-        } else {
-            const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
-            if (FR_OK((int64_t)slot, P0.glist_cap, 18)) starts[slot] = item;
+    constexpr unsigned long long kCellMask = (1ull << 40) - 1;
+    const unsigned lane = threadIdx.x & 31u;
+    // warp-aligned steps: frontier_push needs the whole warp
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < count;
+         i0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = i0 + lane;
+        unsigned long long item = 0;
+        uint32_t start = 0;
+        if (i < count) {
+            item = __ldcg(list + i);
+            const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+            const int64_t cell = (int64_t)(item & kCellMask);
+            const uint32_t deps = g_deps_global<E>(P, cell);
+            if (deps) cnt_set(P, cell, kReadyAt - deps);
+            else start = 0x100u;
         }
+        frontier_push(0, (int64_t)(item & kCellMask), item & ~kCellMask, start, starts, &G->fcount[0],
+                      (unsigned long long)P0.glist_cap);
     }
 }
 
@@ -437,11 +472,10 @@ static __device__ __noinline__ bool grid_barrier(EngineGlobals* G, unsigned nblo
     return s_ok != 0;
 }
 
-// Computes one ready global cell and appends the targets it makes ready.
+// Computes one ready global cell; returns the codes of the targets it makes
+// ready.
 template <class E>
-__device__ __noinline__ void step_round(const Prob& P, int64_t cur, unsigned long long pid_bits,
-                                        unsigned long long* nxt, unsigned long long* ncount,
-                                        unsigned long long cap) {
+__device__ __noinline__ uint32_t step_round(const Prob& P, int64_t cur) {
     walker_compute<E>(P, cur);
     __threadfence();
     const uint32_t tm = g_targets<E>(P, cur);
@@ -453,12 +487,7 @@ __device__ __noinline__ void step_round(const Prob& P, int64_t cur, unsigned lon
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((gm >> k) & 1u) ready |= (uint32_t)(cnt_add(P, cur + offi(k, P.nx), 1u) == kReadyAt) << k;
-    for (; ready; ready &= ready - 1) {
-        const int k = __ffs(ready) - 1;
-        const unsigned long long slot = atomicAdd(ncount, 1ull);
-        if (FR_OK((int64_t)slot, (int64_t)cap, 18))
-            nxt[slot] = pid_bits | (unsigned long long)(cur + offi(k, P.nx));
-    }
+    return ready;
 }
 
 // Frontier buffers: the walker-link region (first problem's link array; the
@@ -481,23 +510,28 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
     const unsigned long long want = (count + blockDim.x - 1) / blockDim.x;
     const unsigned nb = (unsigned)(want < gridDim.x ? want : gridDim.x);
     const unsigned long long stride = (unsigned long long)nb * blockDim.x;
-    const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // lanes walk the lists in warp-aligned steps, so every lane of a warp
+    // runs the same number of steps (frontier_push needs the whole warp)
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane;
     constexpr unsigned long long kCellMask = (1ull << 40) - 1;
     unsigned long long done = 0;
     bool ok = blockIdx.x < nb;
     // first frontier: global cells without global dependencies; the others'
     // counters start at kReadyAt - dependencies
-    if (ok) for (unsigned long long i = first; i < count; i += stride) {
-        const unsigned long long item = __ldcg(buf_b + i);
-        const Prob& P = probs ? probs[(int)(item >> 40)] : single;
-        const int64_t cell = (int64_t)(item & kCellMask);
-        const uint32_t deps = g_deps_global<E>(P, cell);
-        if (deps) {
-            cnt_set(P, cell, kReadyAt - deps);
-            continue;
+    if (ok) for (unsigned long long i0 = first; i0 < count; i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        unsigned long long item = 0;
+        uint32_t start = 0;
+        if (i < count) {
+            item = __ldcg(buf_b + i);
+            const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+            const int64_t cell = (int64_t)(item & kCellMask);
+            const uint32_t deps = g_deps_global<E>(P, cell);
+            if (deps) cnt_set(P, cell, kReadyAt - deps);
+            else start = 0x100u;
         }
-        const unsigned long long slot = atomicAdd(&G->fcount[0], 1ull);
-        if (FR_OK((int64_t)slot, (int64_t)cap, 18)) buf_a[slot] = item;
+        frontier_push(0, (int64_t)(item & kCellMask), item & ~kCellMask, start, buf_a, &G->fcount[0], cap);
     }
     if (ok) ok = grid_barrier(G, nb, limit_ns);
     for (int round = 1; ok; ++round) {
@@ -511,11 +545,19 @@ __global__ void __launch_bounds__(256) k_global_levels(const Prob* __restrict__ 
         // the counter two rounds back is free again: it becomes the next round's
         if (blockIdx.x == 0 && threadIdx.x == 0) G->fcount[(round + 1) % 3] = 0ull;
         unsigned long long* ncount = &G->fcount[round % 3];
-        for (unsigned long long i = first; i < n; i += stride) {
-            const unsigned long long item = __ldcg(cur + i);
-            const Prob& P = probs ? probs[(int)(item >> 40)] : single;
-            step_round<E>(P, (int64_t)(item & kCellMask), item & ~kCellMask, nxt, ncount, cap);
-            ++done;
+        for (unsigned long long i0 = first; i0 < n; i0 += stride) {
+            const unsigned long long i = i0 + lane;
+            unsigned long long item = 0;
+            uint32_t ready = 0;
+            int64_t nx = 0;
+            if (i < n) {
+                item = __ldcg(cur + i);
+                const Prob& P = probs ? probs[(int)(item >> 40)] : single;
+                ready = step_round<E>(P, (int64_t)(item & kCellMask));
+                nx = P.nx;
+                ++done;
+            }
+            frontier_push(nx, (int64_t)(item & kCellMask), item & ~kCellMask, ready, nxt, ncount, cap);
         }
         ok = grid_barrier(G, nb, limit_ns);
     }

@@ -90,13 +90,23 @@ struct SmemHalo {
 };
 constexpr uint16_t kSlotEmpty = 0xFFFFu;
 
-// Marks one global inner cell: its bit and a list entry.
-__device__ __forceinline__ void mark_global_cell(const Prob& P, EngineGlobals* G, int64_t gi,
-                                                 int pid) {
-    atomicOr(P.gbits + (gi >> 5), 1u << (gi & 31));
-    const unsigned long long slot = atomicAdd(&G->glist_count, 1ull);
-    if (FR_OK((int64_t)slot, P.glist_cap, 17))
-        P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
+// Marks the global inner cells of a warp (all 32 lanes call; glob: this
+// lane's cell gi is global): their bits, and list entries reserved with one
+// atomic per warp.
+__device__ __forceinline__ void mark_global_cells(const Prob& P, EngineGlobals* G, int64_t gi,
+                                                  int pid, bool glob) {
+    const unsigned m = __ballot_sync(0xffffffffu, glob);
+    if (!m) return;
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long base = 0;
+    if (lane == (unsigned)(__ffs(m) - 1)) base = atomicAdd(&G->glist_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (glob) {
+        atomicOr(P.gbits + (gi >> 5), 1u << (gi & 31));
+        const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        if (FR_OK((int64_t)slot, P.glist_cap, 17))
+            P.glist[slot] = ((unsigned long long)pid << 40) | (unsigned long long)gi;
+    }
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -442,21 +452,20 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
     }
     __syncthreads();
 
-    // ---- inner tile: publish final cells, list global ones
+    // ---- inner tile: publish final cells, list global ones (every lane of a
+    // warp runs the same steps, as mark_global_cells needs)
     unsigned long long done = 0;
     for (int ly = warp; ly < TY; ly += NW) {
         const int64_t gy = y0 + ly;
-        if (gy >= P.ny) continue;
         for (int lx = lane_id; lx < TX; lx += 32) {
             const int64_t gx = x0 + lx;
-            if (gx >= P.nx) continue;
+            const bool in_grid = gx < P.nx && gy < P.ny;
             const int c = (ly + H) * EX + lx + H;
             const int64_t gi = gy * P.nx + gx;
-            if (S.gf[c]) {
-                mark_global_cell(P, G, gi, pid);
-                continue;
-            }
-            if (S.fin[c] != 1) continue;  // never reached (a cycle in a caller's routing)
+            const bool glob = in_grid && S.gf[c];
+            mark_global_cells(P, G, gi, pid, glob);
+            // cells never reached (a cycle in a caller's routing) stay unpublished
+            if (!in_grid || glob || S.fin[c] != 1) continue;
             ++done;
             wr_f(P.out_hi, P, gi, S.vhi[c], 27);
             // the global phase pulls this trailing word if a target leaves the
