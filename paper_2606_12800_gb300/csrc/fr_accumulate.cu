@@ -126,55 +126,46 @@ __global__ void k_mass_final(const double* __restrict__ partials, int nblocks, d
 
 // ------------------------------------------------------ MFD elevation gradient
 // dL/dz = g^T (dW/dz) w with the lower sets held fixed.  For a source cell c
-// with lower neighbours j: u_j = s_j^p, S = sum u_j, f_j = u_j/S,
-// G = sum f_j g_j, and a_j = w_c (g_j - G)/S * p u_j/(s_j d_j); then
-// dL/dz_c += sum_j a_j and dL/dz_{j} -= a_j.  Each thread gathers the terms
-// that land on its own cell from itself and its eight neighbours.
+// with lower neighbours j: u_j = s_j^p with s_j = (z_c - z_j) / d_j, S = sum
+// u_j, f_j = u_j / S and G = sum f_j g_j.  Then du_j/dz_c = p u_j / (s_j d_j)
+// = p u_j / (z_c - z_j), so the term of edge c -> j is
+//   a_j = w_c (g_j - G) / S * p u_j / (z_c - z_j) = p w_c (g_j - G) f_j / (z_c - z_j),
+// which needs only the stored fractions; dL/dz_c += sum_j a_j and
+// dL/dz_j -= a_j.  Each thread gathers the terms that land on its own cell
+// from itself and its eight neighbours.
 constexpr int GTX = 32, GTY = 16, GNT = 256;
 constexpr int GHX = GTX + 4, GHY = GTY + 4;  // two-cell halo
 
-struct SrcTerms {
-    float a_over_s[8];  // w_c (g_j - G)/S * p/(s_j d_j) * u_j  per code j (0 if not lower)
-};
-
 __device__ __forceinline__ void src_terms(const float* zs, const float* ghs, const float* gls,
-                                          const uint8_t* ms, float w_hi, float w_lo, int hx, int hy,
-                                          const MfdConst& mc, float (&a)[8]) {
+                                          const uint8_t* ms, const float* __restrict__ fr,
+                                          float w_hi, int hx, int hy, float p, float (&a)[8]) {
     const uint32_t m = ms[hy * GHX + hx];
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = 0.0f;
     if (!m) return;
     const float zc = zs[hy * GHX + hx];
-    float u[8];
-    df S = df_make(0.0f);
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(fr));
+    const float4 f1 = __ldg(reinterpret_cast<const float4*>(fr) + 1);
+    float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    df gv[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        u[k] = 0.0f;
-        if ((m >> k) & 1u) {
-            u[k] = mfd_u_call(zc, zs[(hy + offy(k)) * GHX + hx + offx(k)], k, mc);
-            S = df_add(S, df_make(u[k]));
+        gv[k] = df_make(0.0f);
+        if (!((m >> k) & 1u)) {
+            f[k] = 0.0f;
+            continue;
         }
+        const int j = (hy + offy(k)) * GHX + hx + offx(k);
+        gv[k] = {ghs[j], gls[j]};
     }
-    const df inv = df_recip(S);
-    df G = df_make(0.0f);
+    const df G = df_dot8(df_make(0.0f), f, gv);
+    const float pw = __fmul_rn(p, w_hi);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         if (!((m >> k) & 1u)) continue;
-        int j = (hy + offy(k)) * GHX + hx + offx(k);
-        G = df_add(G, df_mul(mfd_frac(u[k], inv), df{ghs[j], gls[j]}));
-    }
-    const df wc = {w_hi, w_lo};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (!((m >> k) & 1u)) continue;
-        int j = (hy + offy(k)) * GHX + hx + offx(k);
-        df dg = df_add(df{ghs[j], gls[j]}, df{-G.hi, -G.lo});
-        float zj = zs[j];
-        float s = __fmul_rn(__fsub_rn(zc, zj), k < 4 ? mc.co_hi : mc.cd_hi);  // s_j
-        float dud_z = __fmul_rn(mc.p, __fdiv_rn(u[k], s));                     // p s^{p-1}/d * ... /(1/d)
-        dud_z = __fmul_rn(dud_z, k < 4 ? mc.co_hi : mc.cd_hi);                  // p s^{p-1} / d
-        df t = df_mul(df_mul(wc, dg), inv);
-        a[k] = __fmul_rn(t.hi, dud_z);
+        const float zj = zs[(hy + offy(k)) * GHX + hx + offx(k)];
+        const float dg = df_add(gv[k], df{-G.hi, -G.lo}).hi;
+        a[k] = __fdividef(__fmul_rn(__fmul_rn(pw, dg), f[k]), __fsub_rn(zc, zj));
     }
 }
 
@@ -205,7 +196,7 @@ __global__ void __launch_bounds__(GNT) k_mfd_grad_z(Prob P, const float* __restr
         float a[8];
         if (gx >= 0 && gy >= 0 && gx < P.nx && gy < P.ny) {
             int64_t gi = gy * P.nx + gx;
-            src_terms(zs, ghs, gls, ms, P.wf[gi], P.wf_lo ? P.wf_lo[gi] : 0.0f, rx + 1, ry + 1, P.mc, a);
+            src_terms(zs, ghs, gls, ms, P.frac + gi * 8, P.wf[gi], rx + 1, ry + 1, P.mc.p, a);
         } else {
 #pragma unroll
             for (int k = 0; k < 8; ++k) a[k] = 0.0f;
