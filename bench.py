@@ -614,8 +614,12 @@ def d8_4096_row(api, L, dev, peak, timed):
 def long_rivers_row(api, L, dev, peak, timed):
     """D8 unit-rain areas on DEMs with long rivers: the D8 DEMs (4096^2 beta 2
     tilt 0.01; 32768^2 beta 2 tilt 0.005) after depression filling, and a
-    32768^2 plane (every row one chain of 32768 cells).  The accumulation call
-    against the roofline at 9 bytes per cell."""
+    32768^2 plane (every row one chain of 32768 cells); the unfilled headline
+    DEM for contrast.  Each input is accumulated with both global phases (cell
+    walkers, tile skeleton) and with the automatic choice between them (the
+    skeleton when the local phase leaves at least 1/512 of the cells); the
+    areas of the three runs must agree bit for bit.  Accumulation against the
+    roofline at 9 bytes per cell."""
     import ctypes
 
     import torch
@@ -626,23 +630,36 @@ def long_rivers_row(api, L, dev, peak, timed):
     def one(name, z):
         n_y, n_x = z.shape
         d = api.receivers_d8(z, DX)
-        area = torch.empty((n_y, n_x), dtype=torch.int64, device=dev)
         ws = api.workspace(n_x, n_y, dev)
-        R = api.routing_d8(d)
+        ref = None
+        row = {}
+        for label, fl in (("auto", 0), ("walkers", _lib.FR_GLOBAL_WALKERS),
+                          ("skeleton", _lib.FR_GLOBAL_SKELETON)):
+            area = torch.empty((n_y, n_x), dtype=torch.int64, device=dev)
+            R = api.routing_d8(d, flags=fl)
 
-        def acc():
-            _lib.check(L.fr_accumulate(ctypes.byref(R), None, None, None, P(area.data_ptr()),
-                                       P(ws.data_ptr()), ws.numel(), api._stream()), "fr_accumulate")
-        ms = timed(acc, reps=3)
-        st = api.get_status(dev)
-        sinks = int(area.view(-1)[d.view(-1) == 0xFF].sum().item())
-        g = ws[:128].cpu().numpy().view("u8")
-        out[name] = {"accumulate_ms": ms, "cells_per_s": n_x * n_y / (ms * 1e-3),
-                     "frac": n_x * n_y * 9 / (ms * 1e-3) / 1e9 / peak, "status": st,
-                     "sink_area_sum_equals_cells": sinks == n_x * n_y,
-                     "global_cells_frac": int(g[4]) / (n_x * n_y),
-                     "max_area": int(area.max().item())}
-        del d, area
+            def acc():
+                _lib.check(L.fr_accumulate(ctypes.byref(R), None, None, None, P(area.data_ptr()),
+                                           P(ws.data_ptr()), ws.numel(), api._stream()), "fr_accumulate")
+            ms = timed(acc, reps=3)
+            st = api.get_status(dev)
+            if ref is None:
+                ref = area
+                sinks = int(area.view(-1)[d.view(-1) == 0xFF].sum().item())
+                g = ws[:128].cpu().numpy().view("u8")
+                share = int(g[4]) / (n_x * n_y)
+                row.update({"sink_area_sum_equals_cells": sinks == n_x * n_y, "global_cells_frac": share,
+                            "chosen": "skeleton" if share >= 1.0 / 512 else "walkers",
+                            "max_area": int(area.max().item())})
+                row.update({"accumulate_ms": ms, "cells_per_s": n_x * n_y / (ms * 1e-3),
+                            "frac": n_x * n_y * 9 / (ms * 1e-3) / 1e9 / peak, "status": st})
+            else:
+                row[label + "_ms"] = ms
+                row[label + "_status"] = st
+                row[label + "_areas_equal"] = bool(torch.equal(area, ref))
+                del area
+        del d, ref
+        out[name] = row
 
     z = inputs.fractal_dem_torch(4096, 4096, beta=2.0, tilt=0.01, seed=SEED, dx=DX, device="cuda")
     F, _ = api.fill(z)
@@ -654,6 +671,7 @@ def long_rivers_row(api, L, dev, peak, timed):
     torch.cuda.empty_cache()
     z = inputs.fractal_dem_torch(N_SIDE, N_SIDE, beta=D8_BETA, tilt=D8_TILT, seed=D8_SEED, dx=DX,
                                  device="cuda")
+    one("rough_32768", z)
     t0 = time.perf_counter()
     F, sweeps = api.fill(z)
     torch.cuda.synchronize()
