@@ -505,16 +505,16 @@ bool encode_tile_map_f32(CUtensorMap* map, const float* base, int64_t nx, int64_
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static Encode fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
+    // the driver's entry point, looked up once (thread-safe static initialisation)
+    static const Encode fn = []() -> Encode {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<Encode>(p);
-        looked = true;
-    }
+            return reinterpret_cast<Encode>(p);
+        return nullptr;
+    }();
     if (!fn || (nx & 3) || ((uintptr_t)base & 15) || nx > (int64_t)1 << 31 || ny > (int64_t)1 << 31) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     const cuuint64_t strides[1] = {(cuuint64_t)nx * 4};

@@ -691,51 +691,51 @@ __global__ void __launch_bounds__(256) k_skel_walk(Prob P, EngineGlobals* G) {
                 if ((old & 0xFFFFull) != 1ull) break;
                 x = q;
             }
-            continue;
-        }
-        for (;;) {
-            const uint8_t k = rd_rb(P, x);
-            const unsigned long long rec = (unsigned long long)__ldcg(
-                reinterpret_cast<const unsigned long long*>(P.link) + x);
-            const int begin = (int)((rec >> 16) & 0xFFFF), len = (int)((rec >> 32) & 0xFFFF);
-            const int64_t yy = x / P.nx, xx = x - yy * P.nx;
-            const int64_t tx = xx / SX, ty = yy / SY;
-            const int64_t ox = tx * SX - 1, oy = ty * SY - 1;  // ring origin of x's tile
-            const uint16_t* pool = P.skpool + (ty * tiles_x + tx) * kSkelPool;
-            df v = df_make(0.0f);
-            unsigned long long a = 0;
-            if constexpr (W) v = df{rd_cg(P.out_hi, P, x, 35), rd_cg(P.out_lo, P, x, 36)};
-            if constexpr (AREA) a = rd_area(P, x);
-#pragma unroll 1
-            for (int s = 0; s < len; ++s) {
-                const int j = __ldcg(pool + begin + s);
-                const int ry = j / SRX, rx = j - ry * SRX;
-                const int64_t y = (oy + ry) * P.nx + (ox + rx);
-                if constexpr (W) v = df_add(v, df{rd_cg(P.out_hi, P, y, 37), rd_cg(P.out_lo, P, y, 38)});
-                if constexpr (AREA) a += rd_area(P, y);
+        } else {
+            for (;;) {
+                const uint8_t k = rd_rb(P, x);
+                const unsigned long long rec = (unsigned long long)__ldcg(
+                    reinterpret_cast<const unsigned long long*>(P.link) + x);
+                const int begin = (int)((rec >> 16) & 0xFFFF), len = (int)((rec >> 32) & 0xFFFF);
+                const int64_t yy = x / P.nx, xx = x - yy * P.nx;
+                const int64_t tx = xx / SX, ty = yy / SY;
+                const int64_t ox = tx * SX - 1, oy = ty * SY - 1;  // ring origin of x's tile
+                const uint16_t* pool = P.skpool + (ty * tiles_x + tx) * kSkelPool;
+                df v = df_make(0.0f);
+                unsigned long long a = 0;
+                if constexpr (W) v = df{rd_cg(P.out_hi, P, x, 35), rd_cg(P.out_lo, P, x, 36)};
+                if constexpr (AREA) a = rd_area(P, x);
+    #pragma unroll 1
+                for (int s = 0; s < len; ++s) {
+                    const int j = __ldcg(pool + begin + s);
+                    const int ry = j / SRX, rx = j - ry * SRX;
+                    const int64_t y = (oy + ry) * P.nx + (ox + rx);
+                    if constexpr (W) v = df_add(v, df{rd_cg(P.out_hi, P, y, 37), rd_cg(P.out_lo, P, y, 38)});
+                    if constexpr (AREA) a += rd_area(P, y);
+                }
+                if constexpr (W) {
+                    wr_f(P.out_hi, P, x, v.hi, 39);
+                    wr_f(P.out_lo, P, x, v.lo, 40);
+                }
+                if constexpr (AREA) wr_area(P, x, a);
+                if (FR_OK(x, ncell(P), 41)) done[x] = 1;
+                // the exit reached from this exit's receiver (an entry of the next tile)
+                if (k >= 8) break;
+                const int64_t s = x + offi(k, P.nx);
+                const unsigned long long rs = (unsigned long long)__ldcg(
+                    reinterpret_cast<const unsigned long long*>(P.link) + s);
+                int64_t q;
+                if ((rs & kLkKind) == kLkExit) q = s;
+                else if ((rs & kLkKind) == kLkEntry) q = (int64_t)(rs & kLkCell);
+                else break;
+                if (!FR_OK(q, ncell(P), 42)) break;
+                // release this exit's value; the completing arrival acquires all
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> at(
+                    reinterpret_cast<unsigned long long*>(P.link)[q]);
+                const unsigned long long old = at.fetch_sub(1ull, cuda::memory_order_acq_rel);
+                if ((old & 0xFFFFull) != 1ull) break;
+                x = q;
             }
-            if constexpr (W) {
-                wr_f(P.out_hi, P, x, v.hi, 39);
-                wr_f(P.out_lo, P, x, v.lo, 40);
-            }
-            if constexpr (AREA) wr_area(P, x, a);
-            if (FR_OK(x, ncell(P), 41)) done[x] = 1;
-            // the exit reached from this exit's receiver (an entry of the next tile)
-            if (k >= 8) break;
-            const int64_t s = x + offi(k, P.nx);
-            const unsigned long long rs = (unsigned long long)__ldcg(
-                reinterpret_cast<const unsigned long long*>(P.link) + s);
-            int64_t q;
-            if ((rs & kLkKind) == kLkExit) q = s;
-            else if ((rs & kLkKind) == kLkEntry) q = (int64_t)(rs & kLkCell);
-            else break;
-            if (!FR_OK(q, ncell(P), 42)) break;
-            // release this exit's value; the completing arrival acquires all
-            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> at(
-                reinterpret_cast<unsigned long long*>(P.link)[q]);
-            const unsigned long long old = at.fetch_sub(1ull, cuda::memory_order_acq_rel);
-            if ((old & 0xFFFFull) != 1ull) break;
-            x = q;
         }
     }
 }
@@ -824,7 +824,6 @@ __global__ void __launch_bounds__(kSkNT, 3) k_skel_fix(Prob P, EngineGlobals* G,
                 const int c = S.gl[i];
                 const int ly = c / SX, lx = c - ly * SX;
                 const int r = (ly + 1) * SRX + lx + 1;
-                const int64_t gi = (g.y0 + ly) * P.nx + g.x0 + lx;
                 uint32_t ext = 0, din = 0, fl = 0;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
