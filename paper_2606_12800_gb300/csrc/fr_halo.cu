@@ -126,6 +126,11 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_c
 // before it.
 __device__ __forceinline__ void queue_push(SmemHalo& S, int c, uint32_t bits, int finished) {
     const unsigned lane = threadIdx.x & 31u;
+    if (!__any_sync(0xffffffffu, bits != 0)) {
+        // the common step: nothing to queue, only finished cells to count
+        if (lane == 0 && finished) atomicAdd(&S.live, -finished);
+        return;
+    }
     const unsigned lt = lanemask_lt();
     const uint32_t n = (uint32_t)__popc(bits);
     // exclusive prefix of n (at most 9) over the lanes, from the ballots of its bits
@@ -399,6 +404,13 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
                     }
                     float f[8];
                     df vv[8];
+                    float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+                    if constexpr (HM::kMfd && HM::kAdj) {
+                        // adjoint: c's own fractions towards its receivers, one 32-byte row
+                        f0 = __ldg(reinterpret_cast<const float4*>(fb));
+                        f1 = __ldg(reinterpret_cast<const float4*>(fb) + 1);
+                    }
+                    const float own[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         f[k] = 0.0f;
@@ -407,10 +419,8 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
                         const int j = c + offy(k) * EX + offx(k);
                         vv[k] = {S.vhi[j], S.vlo[j]};
                         if constexpr (HM::kMfd) {
-                            // forward: the donor's fraction towards c; adjoint:
-                            // c's own fraction towards the receiver
-                            f[k] = HM::kAdj ? __ldg(fb + k)
-                                            : __ldg(fb + offy(k) * row + (offx(k) * 8 + opp(k)));
+                            // forward: the donor's fraction towards c
+                            f[k] = HM::kAdj ? own[k] : __ldg(fb + offy(k) * row + (offx(k) * 8 + opp(k)));
                         } else {
                             f[k] = 1.0f;
                         }

@@ -146,6 +146,56 @@ def test_route_mfd_parity(api, shape, flags):
     assert api.get_status() == 0
 
 
+def test_mfd_dataflow_is_deterministic(api):
+    """The MFD tile solve finalises cells in an order that depends on
+    scheduling, but each cell sums its dependencies in a fixed order: the
+    route and the adjoint must be bit-identical from run to run."""
+    z = inputs.fractal_dem(1500, 1300, beta=2.2, tilt=0.0, seed=17)
+    zt = cuda(z)
+    rain = cuda(inputs.rain_field(1500, 1300, 17))
+    runs = [api.route_mfd(zt, 30.0, 1.1, rain, 0, want_lo=True, want_mask=True) for _ in range(3)]
+    for r in runs[1:]:
+        assert torch.equal(r["w"], runs[0]["w"]) and torch.equal(r["w_lo"], runs[0]["w_lo"])
+    R = api.routing_mfd(runs[0]["mask"], zt, 30.0, 1.1)
+    g1 = api.adjoint(R, runs[0]["w"], runs[0]["w_lo"], want_dz=True)
+    g2 = api.adjoint(R, runs[0]["w"], runs[0]["w_lo"], want_dz=True)
+    assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
+    assert api.get_status() == 0
+
+
+def _bowl(ny, nx, seed):
+    """A bowl with a little seeded roughness: every path converges on the
+    centre, so the tile solves see deep chains and cells that many donors
+    complete at about the same time."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r2 = ((y - ny / 2) ** 2 + (x - nx / 2) ** 2) * 0.01
+    return (r2 + 1e-3 * np.random.default_rng(seed).random((ny, nx))).astype(np.float32)
+
+
+def _plane_x(ny, nx, seed):
+    """A plane falling towards +x with seeded jitter: every cell drains to its
+    three eastern neighbours, so dependencies cross the whole grid."""
+    x = np.arange(nx, dtype=np.float64)[None, :].repeat(ny, 0)
+    return (1000.0 - 0.3 * x + 1e-3 * np.random.default_rng(seed).random((ny, nx))).astype(np.float32)
+
+
+@pytest.mark.parametrize("make", [_bowl, _plane_x])
+@pytest.mark.parametrize("shape", [(130, 140), (300, 517)])
+def test_route_mfd_converging_and_crossing_flows(api, make, shape):
+    ny, nx = shape
+    z = make(ny, nx, ny + nx)
+    rain = inputs.rain_field(ny, nx, 4)
+    out = api.route_mfd(cuda(z), 30.0, 1.1, cuda(rain), 0, want_lo=True, want_mask=True)
+    m_ref, f_ref, w_ref, order = oracle.route_mfd(z, 30.0, 1.1, rain)
+    np.testing.assert_array_equal(out["mask"].cpu().numpy(), m_ref)
+    assert relerr(out["w"].cpu().numpy(), w_ref) <= RTOL_W
+    R = api.routing_mfd(out["mask"], cuda(z), 30.0, 1.1)
+    dLdr, _ = api.adjoint(R, out["w"], out["w_lo"], want_dz=False)
+    g_ref = oracle.adjoint(order, w_ref, frac=f_ref)
+    assert relerr(dLdr.cpu().numpy(), g_ref) <= RTOL_W
+    assert api.get_status() == 0
+
+
 @pytest.mark.parametrize("shape", [(33, 65), (256, 256), (300, 517)])
 def test_adjoint_d8(api, shape):
     ny, nx = shape
