@@ -467,10 +467,11 @@ __global__ void __launch_bounds__(kHaloNT, 2) k_local_halo(Prob Pone, EngineGlob
     unsigned long long done = 0;
     for (int ly = warp; ly < TY; ly += NW) {
         const int64_t gy = y0 + ly;
-        for (int lx = lane_id; lx < TX; lx += 32) {
+        for (int lx0 = 0; lx0 < TX; lx0 += 32) {  // warp-uniform steps
+            const int lx = lx0 + lane_id;
             const int64_t gx = x0 + lx;
-            const bool in_grid = gx < P.nx && gy < P.ny;
-            const int c = (ly + H) * EX + lx + H;
+            const bool in_grid = lx < TX && gx < P.nx && gy < P.ny;
+            const int c = (ly + H) * EX + (lx < TX ? lx : 0) + H;
             const int64_t gi = gy * P.nx + gx;
             const bool glob = in_grid && S.gf[c];
             mark_global_cells(P, G, gi, pid, glob);
