@@ -8,10 +8,15 @@ Cases (all on seeded synthetic fractal DEMs, inputs resident on the device):
   adjoint   slope-split route, then the adjoint of L = sum over sinks of w^2
             (dL/drain and dL/dz)
   fill      depression filling of the D8 DEM (beta 2, tilt 0.01)
+  d8_plane  D8 unit-rain areas on a plane falling towards +x (every row one
+            river of n cells): the global cells go to the tile-skeleton solve
+  d8_filled D8 unit-rain areas on the D8 DEM (beta 2, tilt 0.005) after
+            depression filling: long rivers, the tile-skeleton solve
 Each case runs ``--reps`` times and prints the device status word.
 """
 import argparse
 
+import numpy as np
 import torch
 
 from . import api, inputs
@@ -19,7 +24,7 @@ from . import api, inputs
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=["d8", "d8_area", "mfd", "adjoint", "fill"])
+    ap.add_argument("case", choices=["d8", "d8_area", "mfd", "adjoint", "fill", "d8_plane", "d8_filled"])
     ap.add_argument("--n", type=int, default=4096, help="grid side (n x n)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1)
@@ -29,6 +34,15 @@ def main(argv=None) -> int:
         z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.01, seed=a.seed, device="cuda")
         for _ in range(a.reps):
             api.fill(z)
+    elif a.case in ("d8_plane", "d8_filled"):
+        if a.case == "d8_plane":
+            z = torch.from_numpy(np.ascontiguousarray(inputs.planar_dem(n, n, tilt=0.005, dx=30.0))).to(dev)
+        else:
+            z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.005, seed=a.seed, dx=30.0, device="cuda")
+            z, _ = api.fill(z)
+        R = api.routing_d8(api.receivers_d8(z, 30.0))
+        for _ in range(a.reps):
+            api.accumulate(R, None, want_w=False, want_area=True, device=dev)
     elif a.case.startswith("d8"):
         z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.01, seed=a.seed, device="cuda")
         rain = None if a.case == "d8_area" else inputs.rain_field_torch(n, n, a.seed, device="cuda")
