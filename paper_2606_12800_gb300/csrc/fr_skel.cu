@@ -16,12 +16,16 @@
 //  A. per tile (k_skel_a), in shared memory: every global cell i gets its
 //     in-tile partial value L(i) = c(i) + sum of L over its global donors in
 //     the tile, where c(i) = rain(i) + the final values of its non-global
-//     donors; an entry (a global cell with global donors in other tiles)
-//     learns, by pointer doubling along the in-tile receivers, the exit it
-//     drains to (a global cell whose receiver lies in another tile; D8 paths
-//     are unique), or that its path ends inside the tile.  Each exit x gets
-//     the list of its dependencies: the exits y of neighbouring tiles that
-//     drain into an entry whose path reaches x, in a fixed order.
+//     donors.  Areas alone: by the log-depth chain contraction
+//     (contract_push: pointer jumping along single-donor chains, walkers over
+//     the chains' heads), or, in tiles of long straight chains, by walkers
+//     over the cells (walk_push); with water, by walkers (walk_pull).  An
+//     entry (a global cell with global donors in other tiles) follows the
+//     in-tile receivers to the exit it drains to (a global cell whose
+//     receiver lies in another tile; D8 paths are unique), or to the end of
+//     its path inside the tile.  Each exit x gets the list of its
+//     dependencies: the exits y of neighbouring tiles that drain into an
+//     entry whose path reaches x, in a fixed order.
 //  B. walkers over the exits (k_skel_walk): the total water of an exit is
 //         O(x) = L(x) + sum over its dependencies y of O(y);
 //     an exit with no dependency starts a walker, which computes O(x), then
@@ -29,8 +33,9 @@
 //     an exit's count continues there ("last arriver continues").  One step
 //     crosses a whole tile.
 //  C. per tile again (k_skel_fix): each entry's inflow (the sum of O over its
-//     donors in other tiles) is passed down the in-tile receivers and added
-//     to L of every global cell below it; exits keep O from B.
+//     donors in other tiles) is passed down the in-tile receivers (the same
+//     in-tile solve as A, with the inflows as start values) and added to L of
+//     every global cell below it; exits keep O from B.
 //
 // Sums run in fixed orders (donors in code order, dependency lists in
 // row-major entry order), so results are bit-reproducible; they differ from
@@ -294,6 +299,28 @@ __device__ __forceinline__ void hand_out(S_& S, int nst, int& c, bool& more) {
     if (base + __popc(idle) >= nst) more = false;
 }
 
+// Warp-aggregated hand-out over the global-cell list, keeping only the heads
+// without donors (the starts of contract_push): returns the next one for idle
+// lanes (c < 0), -1 when the list is exhausted.
+template <class S_>
+__device__ __forceinline__ void hand_out_filtered(S_& S, int ng, int& c, bool& more) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned idle = __ballot_sync(0xffffffffu, c < 0);
+    if (!idle) return;
+    const int leader = __ffs(idle) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(&S.head, __popc(idle));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c < 0) {
+        const int i = base + __popc(idle & ((1u << lane) - 1u));
+        if (i < ng) {
+            const int x = S.gl[i];
+            if (S.nin[x] == 0) c = x;
+        }
+    }
+    if (base + __popc(idle) >= ng) more = false;
+}
+
 // Successor word of global cell c (local index; ring index r): its in-tile
 // global receiver, or c itself marked final (and exit if the receiver is a
 // global cell of another tile).
@@ -344,6 +371,146 @@ __device__ void walk_push(S_& S) {
             }
         }
         c = next;
+    }
+}
+
+// In-tile solve over the global cells, areas alone, in O(log L) dependent
+// rounds for chains of length L (log-depth chain contraction).  A global cell
+// with exactly one in-tile global donor is a chain cell; the others are heads
+// (no donor: a start; several: a confluence).  Every chain runs from a head
+// through chain cells to its tail, the last cell before a head, a tile exit or
+// the path's end.
+//   1. Each chain cell's word becomes (value, poison bit 48, donor J in bits
+//      49-60, bit 63 while J is a chain cell).
+//   2. Pointer jumping: a chain cell adds the value and poison of J and takes
+//      J's own J, until J is a head.  Reads and writes of a packed word are
+//      single 64-bit accesses, so every word read pairs a J with the sum from J
+//      (exclusive) to the cell; updates may therefore run in any order.  At
+//      most log2(cells) + 1 rounds; a chain cell still unresolved then lies on
+//      a cycle.
+//   3. Each head learns the tail of its chain (S.qp, indexed by head).
+//   4. Walkers over the heads: a final head's value plus the tail's sum is the
+//      tail's value, which arrives at the tail's receiver (a head): one
+//      arrival (count bits 56-63), its poison (bits 48-55) and its value; the
+//      arrival that completes a head continues there ("last arriver
+//      continues").
+//   5. Every chain cell whose head is final gets the head's value plus its sum.
+// The values are integer sums, so the order of the additions does not matter.
+constexpr unsigned long long kCwChain = 1ull << 63, kCwPois = 1ull << 48;
+// Cells per start from which a tile takes the walk instead of the contraction.
+constexpr int kWalkCellsPerStart = 32;
+__device__ __forceinline__ int cw_j(unsigned long long w) { return (int)((w >> 49) & 0xFFFull); }
+
+template <class S_>
+__device__ void contract_push(S_& S, int ng) {
+    const int tid = threadIdx.x;
+    // 1. chain cells take their donor
+    for (int i = tid; i < ng; i += kSkNT) {
+        const int c = S.gl[i];
+        const uint16_t p = S.sc[c];
+        if (p & kPtrFinal) continue;
+        const int t = p;
+        if (S.nin[t] != 1) continue;
+        const unsigned long long wt = S.pw[t];
+        const bool pois = ((wt >> 48) & 0xFFull) != 0;
+        S.pw[t] = (wt & kPwVal) | (pois ? kCwPois : 0ull) | ((unsigned long long)c << 49) |
+                  (S.nin[c] == 1 ? kCwChain : 0ull);
+    }
+    __syncthreads();
+    // 2. pointer jumping (other threads update words concurrently: volatile
+    // 64-bit accesses, each a single shared-memory transaction, so any word
+    // read is consistent); the block leaves together when no word still
+    // points at a chain cell
+    volatile unsigned long long* vpw = S.pw;
+    for (int round = 0; round < 14; ++round) {
+        int more = 0;
+        for (int i = tid; i < ng; i += kSkNT) {
+            const int c = S.gl[i];
+            if (S.nin[c] != 1) continue;
+            const unsigned long long w = vpw[c];
+            if (!(w & kCwChain)) continue;
+            const unsigned long long wj = vpw[cw_j(w)];
+            const unsigned long long v = ((w & kPwVal) + (wj & kPwVal)) & kPwVal;
+            vpw[c] = v | ((w | wj) & kCwPois) | (wj & (0xFFFull << 49)) | (wj & kCwChain);
+            more |= (wj & kCwChain) != 0;
+        }
+        if (!__syncthreads_or(more)) break;
+    }
+    // 3. tails (S.qp[head] = its chain's tail; a head without a chain is its own)
+    for (int i = tid; i < ng; i += kSkNT) {
+        const int c = S.gl[i];
+        S.qp[c] = (uint16_t)c;
+    }
+    __syncthreads();
+    for (int i = tid; i < ng; i += kSkNT) {
+        const int c = S.gl[i];
+        const uint16_t p = S.sc[c];
+        const bool tail = (p & kPtrFinal) || S.nin[p & 0xFFF] != 1;
+        if (!tail) continue;
+        if (S.nin[c] == 1) {
+            const unsigned long long w = S.pw[c];
+            if (!(w & kCwChain)) S.qp[cw_j(w)] = (uint16_t)c;  // else on a cycle
+        }
+    }
+    __syncthreads();
+    // 4. walkers over the heads; starts are the heads without donors, taken
+    // from the global-cell list
+    {
+        int c = -1;
+        unsigned long long w = 0;
+        bool more = true;
+        for (;;) {
+            if (more) {
+                const int was = c;
+                hand_out_filtered(S, ng, c, more);
+                if (was < 0 && c >= 0) w = S.pw[c];
+            }
+            // entries that are not starts leave lanes idle: stop only when
+            // the list is exhausted too (more is warp-uniform)
+            if (!__any_sync(0xffffffffu, c >= 0)) {
+                if (!more) break;
+                continue;
+            }
+            if (c < 0) continue;
+            // the tail of c's chain and its value
+            const int tl = S.qp[c];
+            unsigned long long v = w & kPwVal, pois = (w >> 48) & 0xFFull;
+            if (tl != c) {
+                const unsigned long long wt = S.pw[tl];
+                v = (v + (wt & kPwVal)) & kPwVal;
+                pois |= wt & kCwPois;
+            }
+            const uint16_t p = S.sc[tl];
+            int next = -1;
+            if (!(p & kPtrFinal)) {
+                const int t = p;
+                const unsigned long long add = kPwOne | (pois ? kPwPois : 0ull) | v;
+                const unsigned long long old = atomicAdd(&S.pw[t], add);
+                if ((old >> 56) == kDone - 1) {
+                    next = t;
+                    w = old + add;
+                }
+            }
+            c = next;
+        }
+    }
+    __syncthreads();
+    // 5. chain cells: the head's value plus their sums (only heads are read,
+    // only chain cells written)
+    for (int i = tid; i < ng; i += kSkNT) {
+        const int c = S.gl[i];
+        if (S.nin[c] != 1) continue;
+        const unsigned long long w = S.pw[c];
+        unsigned long long out = 0;  // unfinished (on or below a cycle)
+        if (!(w & kCwChain)) {
+            const unsigned long long wh = S.pw[cw_j(w)];
+            if ((wh >> 56) == kDone) {
+                const bool pois = (((wh >> 48) & 0xFFull) != 0) || (w & kCwPois);
+                out = (unsigned long long)kDone << 56 | (pois ? kPwPois : 0ull) |
+                      (((wh & kPwVal) + (w & kPwVal)) & kPwVal);
+            }
+        }
+        S.pw[c] = out;
     }
 }
 
@@ -504,8 +671,15 @@ __global__ void __launch_bounds__(kSkNT, 3) k_skel_a(Prob P, EngineGlobals* G) {
             push_start(S, start);
         }
         __syncthreads();
-        if constexpr (kPush) walk_push(S);
-        else walk_pull<AREA>(S);
+        if constexpr (kPush) {
+            // long straight chains (many cells per start): the walk does n
+            // steps and its depth is hidden by the other blocks on the SM;
+            // else the log-depth contraction
+            if (ng >= kWalkCellsPerStart * S.qtail) walk_push(S);
+            else contract_push(S, ng);
+        } else {
+            walk_pull<AREA>(S);
+        }
         __syncthreads();
         // ---- where each boundary cell's in-tile path ends (one thread per
         // boundary cell follows the successor words; at most ng steps, so a
@@ -857,8 +1031,15 @@ __global__ void __launch_bounds__(kSkNT, 3) k_skel_fix(Prob P, EngineGlobals* G,
             push_start(S, start);
         }
         __syncthreads();
-        if constexpr (kPush) walk_push(S);
-        else walk_pull<AREA>(S);
+        if constexpr (kPush) {
+            // long straight chains (many cells per start): the walk does n
+            // steps and its depth is hidden by the other blocks on the SM;
+            // else the log-depth contraction
+            if (ng >= kWalkCellsPerStart * S.qtail) walk_push(S);
+            else contract_push(S, ng);
+        } else {
+            walk_pull<AREA>(S);
+        }
         __syncthreads();
         // final values: L (pass A, in the outputs) plus the inflow sums, in
         // batches of eight cells per thread whose loads are issued together

@@ -54,6 +54,10 @@ def _check(api, z, flags, rain, variants=VARIANTS):
         w, lo = out["w"].cpu().numpy(), out["w_lo"].cpu().numpy()
         assert relerr(w, w_ref) <= RTOL_W, v
         assert relerr(w.astype(np.float64) + lo, w_ref) <= 1e-10, v
+        # areas alone: the skeleton's integer solve (chain contraction)
+        out = api.route_d8(zt, 30.0, None, flags | v, want_w=False, want_area=True)
+        assert api.get_status() == 0, v
+        np.testing.assert_array_equal(out["area"].cpu().numpy().astype(np.uint64), a_ref)
     return a_ref
 
 
@@ -114,6 +118,8 @@ def test_skeleton_is_bit_reproducible(api):
         b = api.route_d8(zt, 30.0, rt, SKEL, want_w=True, want_lo=True, want_area=True)
         for k in ("w", "w_lo", "area"):
             assert torch.equal(a[k], b[k]), k
+        c = api.route_d8(zt, 30.0, None, SKEL, want_w=False, want_area=True)
+        assert torch.equal(a["area"], c["area"])
 
 
 @pytest.mark.parametrize("variant", [SKEL, WALK])
@@ -131,6 +137,8 @@ def test_cycles_report_no_progress(api, variant):
     d[150, 150], d[150, 151] = 0, 2      # ... into a 2-cycle
     R = api.routing_d8(cuda(d), variant)
     api.accumulate(R, None, want_w=True, want_area=True)
+    assert api.get_status() == 5
+    api.accumulate(R, None, want_w=False, want_area=True)  # areas alone
     assert api.get_status() == 5
     z = inputs.planar_dem(ny, nx, 0.01, 30.0)
     api.route_d8(cuda(z), 30.0, None, variant)
@@ -155,6 +163,9 @@ def test_eight_donor_lattice_forced_skeleton(api):
     assert api.get_status() == 0
     np.testing.assert_array_equal(o["area"].cpu().numpy().astype(np.uint64), a_ref)
     assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
+    o = api.accumulate(R, None, want_w=False, want_area=True)  # areas alone
+    assert api.get_status() == 0
+    np.testing.assert_array_equal(o["area"].cpu().numpy().astype(np.uint64), a_ref)
 
 
 def test_global_phase_flags_are_validated(api):
