@@ -8,10 +8,11 @@
 // receivers per cell (App. A) dependency sets spread wider than D8 basins, so
 // the halo is deeper: at 64x32 + 8 about 0.9 % of the cells of a rough
 // fractal DEM stay global, against about 21 % for the same tiles without a
-// halo.  The tiles are 64x64 (two blocks of about 96 KB per SM): measured
-// 14 % faster per 8192^2 route than 64x32 (three blocks per SM), which has
-// 1.875 region cells per inner cell against 1.56; halos of 6 and 10 cells
-// were slower than 8.
+// halo.  The tiles are 64x64 (two blocks of about 103 KB and 384 threads per
+// SM, 1.56 region cells per inner cell): smaller tiles that fit more blocks
+// per SM (64x32, 48x48, 56x48, 40x40) were measured slower, their extra halo
+// cells costing more than the occupancy gains; halos of 6 and 10 cells were
+// slower than 8.
 //
 // The three modes differ only in the direction of the dependencies:
 //   forward MFD   w_c = r_c    + sum over donors j    of f_{j->c} w_j
