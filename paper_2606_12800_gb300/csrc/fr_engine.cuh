@@ -603,7 +603,10 @@ cudaError_t launch_global(const Prob* probs, const Prob& single, EngineGlobals* 
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_global_levels<M, W, AREA>, 256, 0);
             if (e != cudaSuccess) return e;
             if (per < 1) return cudaErrorInvalidConfiguration;
-            grid = sms * (per < 4 ? per : 4);
+            // one block per SM: a round's frontier (about 20 K cells on an 8192^2
+            // slope-split route) fits, and the grid barrier has the fewest
+            // arrivals (measured faster than two or four blocks per SM)
+            grid = sms;
             if (dev < 64) grid_of[dev] = grid;
         }
         Prob one = single;
