@@ -4,6 +4,7 @@ chosen size (``ncu -k ...  python -m paper_2606_12800_gb300.cases mfd --n 4096``
 Cases (all on seeded synthetic fractal DEMs, inputs resident on the device):
   d8        receivers + D8 accumulation with rain U[0,1) (two-float w, uint64 areas)
   d8_area   receivers + D8 unit-rain areas only
+  d8_step   receivers + D8 unit-rain areas + the mass balance (the benchmark step)
   mfd       slope-split route (p = 1.1), unit rain
   adjoint   slope-split route, then the adjoint of L = sum over sinks of w^2
             (dL/drain and dL/dz)
@@ -24,7 +25,8 @@ from . import api, inputs
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=["d8", "d8_area", "mfd", "adjoint", "fill", "d8_plane", "d8_filled"])
+    ap.add_argument("case", choices=["d8", "d8_area", "d8_step", "mfd", "adjoint", "fill", "d8_plane",
+                                     "d8_filled"])
     ap.add_argument("--n", type=int, default=4096, help="grid side (n x n)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1)
@@ -45,12 +47,14 @@ def main(argv=None) -> int:
             api.accumulate(R, None, want_w=False, want_area=True, device=dev)
     elif a.case.startswith("d8"):
         z = inputs.fractal_dem_torch(n, n, beta=2.0, tilt=0.01, seed=a.seed, device="cuda")
-        rain = None if a.case == "d8_area" else inputs.rain_field_torch(n, n, a.seed, device="cuda")
+        rain = None if a.case in ("d8_area", "d8_step") else inputs.rain_field_torch(n, n, a.seed, device="cuda")
         d = api.receivers_d8(z, 30.0)
         R = api.routing_d8(d)
         for _ in range(a.reps):
             api.receivers_d8(z, 30.0)
-            api.accumulate(R, rain, want_w=rain is not None, want_area=True, device=dev)
+            out = api.accumulate(R, rain, want_w=rain is not None, want_area=True, device=dev)
+            if a.case == "d8_step":
+                api.mass_balance(R, area=out["area"], device=dev)
     else:
         z = inputs.fractal_dem_torch(n, n, beta=2.2, tilt=0.0, seed=a.seed, device="cuda")
         for _ in range(a.reps):
