@@ -700,9 +700,22 @@ def adjoint_row(api, dev, peak, timed):
         return api.adjoint(R, fwd["w"], fwd["w_lo"], want_dz=True)
     ms = timed(adj, reps=3)
     status = api.get_status(dev)
-    del zt, m, fwd
+    # the same adjoint reading the fractions the forward left in a workspace
+    # of its own (FR_WEIGHTS_IN_WORKSPACE) instead of recomputing them
+    import torch
+    from paper_2606_12800_gb300 import _lib
+    ws = torch.empty(api.workspace_size(n, n, mfd=True), dtype=torch.uint8, device=dev)
+    fwd = api.accumulate(R, None, want_w=True, want_lo=True, device=dev, ws=ws)
+    Rk = api.routing_mfd(m, zt, DX, 1.1, _lib.FR_WEIGHTS_IN_WORKSPACE)
+
+    def adj_kept():
+        return api.adjoint(Rk, fwd["w"], fwd["w_lo"], want_dz=True, ws=ws)
+    ms_kept = timed(adj_kept, reps=3)
+    status |= api.get_status(dev, ws=ws)
+    del zt, m, fwd, ws
     # algorithmic bytes: z 4 + w 4 in, dL/dr 4 + dL/dz 4 out
-    return {"ms": ms, "value": n * n / (ms * 1e-3), "unit": "cells/s", "status": status,
+    return {"ms": ms, "kept_weights_ms": ms_kept, "value": n * n / (ms * 1e-3), "unit": "cells/s",
+            "status": status,
             "workload": "MFD p=1.1 adjoint alone (dL/drain and dL/dz) of L = sum over sinks of "
                         "w^2, %dx%d fractal DEM beta=2.2" % (n, n),
             "hbm_frac": (n * n * 16) / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_cell": 16}

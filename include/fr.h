@@ -98,6 +98,19 @@ typedef enum {
  *   FR_GLOBAL_WALKERS  always the cell walkers.
  *   FR_GLOBAL_SKELETON always the skeleton solve (grids too small for its
  *                  scratch, under about 64x64 cells, use the walkers).
+ * Routing flag of MFD routings (fr_routing.flags), for fr_accumulate and
+ * fr_route_adjoint: the checkpoint of the weights between a forward route and
+ * its adjoint.  By default both calls recompute the fractions from the DEM
+ * into the workspace (a stored copy would take 32 bytes per cell).
+ *   FR_WEIGHTS_IN_WORKSPACE  the workspace already holds this routing's
+ *                  fractions: fr_route_mfd, fr_accumulate or fr_route_adjoint
+ *                  left them there, called with the same routing (mask, DEM,
+ *                  dx, p and the receiver flags) and the same workspace, and
+ *                  no call on a different routing used that workspace since.
+ *                  The call reads them instead of recomputing them.  The
+ *                  library cannot check this; wrong fractions give wrong
+ *                  results, not an error.  D8 routings and the receiver,
+ *                  fused route and batch calls reject this flag.
  */
 #define FR_EDGE_SINK 0x0u
 #define FR_EDGE_ROUTE 0x1u
@@ -108,6 +121,7 @@ typedef enum {
 #define FR_DINF 0x10u
 #define FR_GLOBAL_WALKERS 0x20u
 #define FR_GLOBAL_SKELETON 0x40u
+#define FR_WEIGHTS_IN_WORKSPACE 0x80u
 
 #define FR_SINK 0xFFu
 

@@ -13,8 +13,8 @@ from typing import Dict, Optional
 import torch
 
 from . import _lib
-from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_FILL, FR_OP_MFD, FR_OP_ROUTE, check,
-                   fr_routing, load)
+from ._lib import (FR_ROUTING_D8, FR_ROUTING_MFD, FR_OP_FILL, FR_OP_MFD, FR_OP_ROUTE,
+                   FR_WEIGHTS_IN_WORKSPACE, check, fr_routing, load)
 
 # one workspace per (device, stream): calls on different streams may overlap
 _ws_cache: Dict[tuple, torch.Tensor] = {}
@@ -44,15 +44,21 @@ def workspace(nx: int, ny: int, device=None, mfd: bool = False) -> torch.Tensor:
     (with room for the fractions of an MFD routing when ``mfd``)."""
     dev = torch.device(device if device is not None else "cuda")
     idx = dev.index if dev.index is not None else torch.cuda.current_device()
-    need = int(load().fr_workspace_size(FR_OP_MFD if mfd else FR_OP_ROUTE, nx, ny, 0))
-    if need == 0:
-        raise ValueError("invalid grid size %dx%d" % (nx, ny))
+    need = workspace_size(nx, ny, mfd)
     key = (idx, torch.cuda.current_stream(torch.device("cuda", idx)).cuda_stream)
     ws = _ws_cache.get(key)
     if ws is None or ws.numel() < need:
         ws = torch.empty(need, dtype=torch.uint8, device=torch.device("cuda", idx))
         _ws_cache[key] = ws
     return ws
+
+
+def workspace_size(nx: int, ny: int, mfd: bool = False) -> int:
+    """Bytes of a workspace for any operation on an nx-by-ny grid (fr_workspace_size)."""
+    need = int(load().fr_workspace_size(FR_OP_MFD if mfd else FR_OP_ROUTE, nx, ny, 0))
+    if need == 0:
+        raise ValueError("invalid grid size %dx%d" % (nx, ny))
+    return need
 
 
 def routing_d8(dir_: torch.Tensor, flags: int = 0) -> fr_routing:
@@ -110,8 +116,11 @@ def receivers_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1, flags: in
 
 
 def accumulate(R: fr_routing, rain: Optional[torch.Tensor] = None, want_w: bool = True,
-               want_lo: bool = False, want_area: bool = False, device=None) -> Dict[str, torch.Tensor]:
-    """Water per cell for a routing (D8 or MFD); see fr_accumulate."""
+               want_lo: bool = False, want_area: bool = False, device=None,
+               ws: Optional[torch.Tensor] = None) -> Dict[str, torch.Tensor]:
+    """Water per cell for a routing (D8 or MFD); see fr_accumulate.  ws: a
+    workspace of the caller's (workspace_size bytes), e.g. to keep the MFD
+    fractions for a later adjoint (FR_WEIGHTS_IN_WORKSPACE)."""
     ny, nx = R.ny, R.nx
     dev = device or torch.device("cuda", torch.cuda.current_device())
     if rain is not None:
@@ -121,7 +130,8 @@ def accumulate(R: fr_routing, rain: Optional[torch.Tensor] = None, want_w: bool 
     w = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_w else None
     lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
     a = torch.empty((ny, nx), dtype=torch.int64, device=dev) if want_area else None
-    ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
+    if ws is None:
+        ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
     check(load().fr_accumulate(ctypes.byref(R), _p(rain), _p(w), _p(lo), _p(a), _p(ws),
                                ws.numel(), _stream()), "fr_accumulate")
     if w is not None:
@@ -175,8 +185,10 @@ def route_d8(dem: torch.Tensor, dx: float = 30.0, rain: Optional[torch.Tensor] =
 
 def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
               rain: Optional[torch.Tensor] = None, flags: int = 0, want_lo: bool = False,
-              want_mask: bool = False) -> Dict[str, torch.Tensor]:
-    """Receivers + accumulation (MFD) in one call (fr_route_mfd)."""
+              want_mask: bool = False, ws: Optional[torch.Tensor] = None) -> Dict[str, torch.Tensor]:
+    """Receivers + accumulation (MFD) in one call (fr_route_mfd).  ws: a
+    workspace of the caller's (workspace_size(nx, ny, mfd=True) bytes), which
+    then keeps the fractions for a later adjoint (FR_WEIGHTS_IN_WORKSPACE)."""
     dem_d, host = _to_cuda(dem)
     rain_d, _ = _to_cuda(rain)
     _check_grid(dem_d, torch.float32, "dem")
@@ -185,7 +197,8 @@ def route_mfd(dem: torch.Tensor, dx: float = 30.0, p: float = 1.1,
     w = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     lo = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_lo else None
     m = torch.empty((ny, nx), dtype=torch.uint8, device=dev) if want_mask else None
-    ws = workspace(nx, ny, dev, mfd=True)
+    if ws is None:
+        ws = workspace(nx, ny, dev, mfd=True)
     check(load().fr_route_mfd(_p(dem_d), nx, ny, dx, p, flags, _p(rain_d), _p(w), _p(lo), _p(m),
                               _p(ws), ws.numel(), _stream()), "fr_route_mfd")
     out = {k: v for k, v in (("w", w), ("w_lo", lo), ("mask", m)) if v is not None}
@@ -230,14 +243,18 @@ def fill(dem: torch.Tensor, max_sweeps: int = 100000, flags: int = 0):
 
 
 def adjoint(R: fr_routing, w: torch.Tensor, w_lo: Optional[torch.Tensor] = None,
-            dLdw: Optional[torch.Tensor] = None, want_dz: bool = False):
+            dLdw: Optional[torch.Tensor] = None, want_dz: bool = False,
+            ws: Optional[torch.Tensor] = None):
     """(dL/dr, dL/dz or None) for L = sum over sinks of w^2, or for the
-    incoming gradient dLdw (fr_route_adjoint)."""
+    incoming gradient dLdw (fr_route_adjoint).  ws: a workspace of the
+    caller's; with FR_WEIGHTS_IN_WORKSPACE in R.flags it must hold R's
+    fractions from the forward call."""
     ny, nx = R.ny, R.nx
     dev = w.device
     dLdr = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     dLdz = torch.empty((ny, nx), dtype=torch.float32, device=dev) if want_dz else None
-    ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
+    if ws is None:
+        ws = workspace(nx, ny, dev, mfd=R.kind == FR_ROUTING_MFD)
     check(load().fr_route_adjoint(ctypes.byref(R), _p(w), _p(w_lo), _p(dLdw), _p(dLdr), _p(dLdz),
                                   _p(ws), ws.numel(), _stream()), "fr_route_adjoint")
     return dLdr, dLdz
@@ -253,12 +270,13 @@ def mass_balance(R: fr_routing, rain=None, w=None, w_lo=None, area=None, device=
     return out
 
 
-def get_status(device=None) -> int:
+def get_status(device=None, ws: Optional[torch.Tensor] = None) -> int:
     """Synchronises the current stream and returns (and clears) the device
-    status word of the cached workspace (0 = ok)."""
-    dev = torch.device(device if device is not None else "cuda")
-    idx = dev.index if dev.index is not None else torch.cuda.current_device()
-    ws = _ws_cache.get((idx, torch.cuda.current_stream(torch.device("cuda", idx)).cuda_stream))
+    status word of the workspace ws, by default the cached one (0 = ok)."""
+    if ws is None:
+        dev = torch.device(device if device is not None else "cuda")
+        idx = dev.index if dev.index is not None else torch.cuda.current_device()
+        ws = _ws_cache.get((idx, torch.cuda.current_stream(torch.device("cuda", idx)).cuda_stream))
     if ws is None:
         return 0
     return int(load().fr_get_status(_p(ws), ws.numel(), _stream()))
@@ -283,15 +301,27 @@ def set_wait_limit(ns: int) -> int:
 
 class RouteMFD(torch.autograd.Function):
     """w = route_mfd(dem, rain) with a hand-written adjoint backward
-    (gradients with respect to the elevations and the rain)."""
+    (gradients with respect to the elevations and the rain).
+
+    keep_weights: keep the forward's workspace, with its 32 B/cell fractions,
+    until the backward, which then reads the fractions instead of recomputing
+    them from the DEM and the mask (FR_WEIGHTS_IN_WORKSPACE).  By default
+    only the DEM, the mask and the two-float water are kept (13 B/cell) and
+    the backward recomputes the fractions: the checkpoint of the weights."""
 
     @staticmethod
-    def forward(ctx, dem, rain, dx: float = 30.0, p: float = 1.1, flags: int = 0):
+    def forward(ctx, dem, rain, dx: float = 30.0, p: float = 1.1, flags: int = 0,
+                keep_weights: bool = False):
         mask = receivers_mfd(dem, dx, p, flags)
         R = routing_mfd(mask, dem, dx, p, flags)
-        out = accumulate(R, rain, want_w=True, want_lo=True, device=dem.device)
+        ws = None
+        if keep_weights:
+            ny, nx = dem.shape
+            ws = torch.empty(workspace_size(nx, ny, mfd=True), dtype=torch.uint8, device=dem.device)
+        out = accumulate(R, rain, want_w=True, want_lo=True, device=dem.device, ws=ws)
         ctx.save_for_backward(dem, mask, out["w"], out["w_lo"])
         ctx.cfg = (dx, p, flags)
+        ctx.ws = ws
         return out["w"]
 
     @staticmethod
@@ -301,10 +331,12 @@ class RouteMFD(torch.autograd.Function):
         want_dz = ctx.needs_input_grad[0]
         want_dr = ctx.needs_input_grad[1]
         if not (want_dz or want_dr):
-            return None, None, None, None, None
-        R = routing_mfd(mask, dem, dx, p, flags)
-        dLdr, dLdz = adjoint(R, w, w_lo, dLdw=grad_w.contiguous().float(), want_dz=want_dz)
-        return (dLdz if want_dz else None), (dLdr if want_dr else None), None, None, None
+            return None, None, None, None, None, None
+        kept = ctx.ws is not None
+        R = routing_mfd(mask, dem, dx, p, flags | (FR_WEIGHTS_IN_WORKSPACE if kept else 0))
+        dLdr, dLdz = adjoint(R, w, w_lo, dLdw=grad_w.contiguous().float(), want_dz=want_dz, ws=ctx.ws)
+        ctx.ws = None
+        return (dLdz if want_dz else None), (dLdr if want_dr else None), None, None, None, None
 
 
 def route_batch(dems, rains=None, kind: str = "d8", dx: float = 30.0, p: float = 1.1,

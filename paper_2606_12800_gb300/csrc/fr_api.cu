@@ -16,7 +16,10 @@ namespace {
 constexpr int64_t kMaxCells = (int64_t)1 << 40;
 constexpr int kMassBlocks = 1024;
 constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE | FR_D4 | FR_DINF |
-                                 FR_GLOBAL_WALKERS | FR_GLOBAL_SKELETON;
+                                 FR_GLOBAL_WALKERS | FR_GLOBAL_SKELETON | FR_WEIGHTS_IN_WORKSPACE;
+// flags of the receiver and fused route calls: the weights flag describes a
+// routing's workspace and has no meaning there
+constexpr uint32_t kCallFlags = kKnownFlags & ~FR_WEIGHTS_IN_WORKSPACE;
 
 // D8 forward: the global phase switches from the cell walkers to the
 // tile-skeleton solve when the local phase leaves at least this share of the
@@ -107,7 +110,8 @@ bool routing_ok(const fr_routing* R) {
     if (!R || R->reserved || R->reserved2) return false;
     if (!sizes_ok(R->nx, R->ny)) return false;
     if (R->kind == FR_ROUTING_D8)
-        return R->dir != nullptr && !(R->flags & FR_DINF) && (R->flags & ~kKnownFlags) == 0 &&
+        return R->dir != nullptr && !(R->flags & (FR_DINF | FR_WEIGHTS_IN_WORKSPACE)) &&
+               (R->flags & ~kKnownFlags) == 0 &&
                (R->flags & (FR_GLOBAL_WALKERS | FR_GLOBAL_SKELETON)) != (FR_GLOBAL_WALKERS | FR_GLOBAL_SKELETON);
     if (R->kind == FR_ROUTING_MFD)
         return R->mask && R->dem && std::isfinite(R->dx) && R->dx > 0 && std::isfinite(R->p) &&
@@ -224,7 +228,7 @@ fr_status fr_get_status(const void* ws, size_t ws_bytes, void* stream) {
 fr_status fr_receivers_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
                           uint8_t* dir_out, uint8_t* indeg_out, void* stream) {
     if (!dem || !dir_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
-        (flags & ~kKnownFlags) || (flags & FR_DINF))
+        (flags & ~kCallFlags) || (flags & FR_DINF))
         return FR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (flags & FR_CHECK_FINITE) {
@@ -238,7 +242,7 @@ fr_status fr_receivers_mfd(const float* dem, int64_t nx, int64_t ny, double dx, 
                            uint32_t flags, uint8_t* mask_out, float* frac_out, uint8_t* indeg_out,
                            void* stream) {
     if (!dem || !mask_out || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 ||
-        !std::isfinite(p) || p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags) ||
+        !std::isfinite(p) || p <= 0 || p > FR_MFD_MAX_P || (flags & ~kCallFlags) ||
         (flags & FR_D4))
         return FR_ERR_INVALID_ARG;
     if (frac_out && ((uintptr_t)frac_out & 15)) return FR_ERR_INVALID_ARG;
@@ -281,7 +285,7 @@ fr_status accumulate_impl(const fr_routing* R, const float* rain, float* w_out, 
     if (e != cudaSuccess) return FR_ERR_CUDA;
     EngineGlobals* G = reinterpret_cast<EngineGlobals*>(ws);
     if (!mfd) return cuda_status(launch_d8_forward(w_out != nullptr, area_out != nullptr, P, G, s));
-    if (!fracs_ready) {
+    if (!fracs_ready && !(R->flags & FR_WEIGHTS_IN_WORKSPACE)) {
         e = launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p, R->flags,
                                  reinterpret_cast<float*>((char*)ws + L.frac), s);
         if (e != cudaSuccess) return FR_ERR_CUDA;
@@ -394,7 +398,7 @@ fr_status fr_accumulate_richardson(const fr_routing* R, const float* rain, float
 fr_status fr_route_d8(const float* dem, int64_t nx, int64_t ny, double dx, uint32_t flags,
                       const float* rain, float* w_out, float* w_lo_out, uint64_t* area_out,
                       uint8_t* dir_out, void* ws, size_t ws_bytes, void* stream) {
-    if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || (flags & ~kKnownFlags) ||
+    if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || (flags & ~kCallFlags) ||
         (flags & FR_DINF))
         return FR_ERR_INVALID_ARG;
     if (!ws_ok(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
@@ -416,7 +420,7 @@ fr_status fr_route_mfd(const float* dem, int64_t nx, int64_t ny, double dx, doub
                        uint32_t flags, const float* rain, float* w_out, float* w_lo_out,
                        uint8_t* mask_out, void* ws, size_t ws_bytes, void* stream) {
     if (!dem || !sizes_ok(nx, ny) || !std::isfinite(dx) || dx <= 0 || !std::isfinite(p) ||
-        p <= 0 || p > FR_MFD_MAX_P || (flags & ~kKnownFlags) || (flags & FR_D4))
+        p <= 0 || p > FR_MFD_MAX_P || (flags & ~kCallFlags) || (flags & FR_D4))
         return FR_ERR_INVALID_ARG;
     if (!ws_ok_mfd(ws, ws_bytes, nx * ny)) return FR_ERR_WORKSPACE;
     const Layout L = layout(nx * ny);
@@ -457,8 +461,9 @@ fr_status fr_route_adjoint(const fr_routing* R, const float* w, const float* w_l
     P.lo_full = dLdz_out ? 1 : 0;  // the elevation gradient reads every trailing word
     const Layout L = layout(n);
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return FR_ERR_CUDA;
-    if (mfd && launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p, R->flags,
-                                    reinterpret_cast<float*>((char*)ws + L.frac), s) != cudaSuccess)
+    if (mfd && !(R->flags & FR_WEIGHTS_IN_WORKSPACE) &&
+        launch_mfd_fractions(R->dem, R->mask, R->nx, R->ny, R->dx, R->p, R->flags,
+                             reinterpret_cast<float*>((char*)ws + L.frac), s) != cudaSuccess)
         return FR_ERR_CUDA;
     cudaError_t e = launch_adjoint(mfd, P, reinterpret_cast<EngineGlobals*>(ws), s);
     if (e != cudaSuccess) return FR_ERR_CUDA;

@@ -42,7 +42,7 @@ def test_workspace_size(lib):
     assert n >= 4096 * 4096 * 13
     assert n % 256 == 0
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 0, 10, 0) == 0
-    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 10, 10, 0x80) == 0
+    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 10, 10, 0x100) == 0  # an unknown flag
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 1 << 21, 1 << 21, 0) == 0  # > 2^40 cells
     # MFD operations keep 8 fp32 fractions per cell on top of the common part
     m = lib.fr_workspace_size(_lib.FR_OP_MFD, 4096, 4096, 0)
@@ -132,3 +132,23 @@ def test_batch_and_global_phase_flags_validation(lib):
     fake = P(0x1000)
     assert lib.fr_accumulate(ctypes.byref(R), None, None, None, fake, fake, 1 << 20, None) == \
         _lib.FR_ERR_INVALID_ARG
+
+
+def test_weights_flag_only_for_mfd_routings(lib):
+    """FR_WEIGHTS_IN_WORKSPACE describes an MFD routing's workspace: D8
+    routings, the receiver calls and the fused routes reject it."""
+    fake = ctypes.c_void_p(0x1000)
+    W = _lib.FR_WEIGHTS_IN_WORKSPACE
+    R = _lib.fr_routing()
+    R.kind, R.nx, R.ny, R.dir, R.flags = _lib.FR_ROUTING_D8, 8, 8, 0x1000, W
+    assert lib.fr_accumulate(ctypes.byref(R), None, None, None, fake, fake, 1 << 20, None) == \
+        _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_route_adjoint(ctypes.byref(R), fake, None, None, fake, None, fake, 1 << 20,
+                                None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_d8(fake, 8, 8, 30.0, W, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_mfd(fake, 8, 8, 30.0, 1.1, W, fake, None, None, None) == \
+        _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_route_d8(fake, 8, 8, 30.0, W, None, fake, None, None, None, fake, 1 << 20,
+                           None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_route_mfd(fake, 8, 8, 30.0, 1.1, W, None, fake, None, None, fake, 1 << 20,
+                            None) == _lib.FR_ERR_INVALID_ARG

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2606_12800_gb300 import inputs
+from paper_2606_12800_gb300 import _lib, inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -592,6 +592,45 @@ def test_dinf_batch_adjoint_and_large_route(api):
         m_ref, _, w_ref, _ = oracle.route_mfd(d, 30.0, 1.1, r, oracle.DINF)
         np.testing.assert_array_equal(o["route"].cpu().numpy(), m_ref)
         assert relerr(o["w"].cpu().numpy(), w_ref) <= RTOL_W
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (300, 517)])
+def test_adjoint_mfd_kept_weights(api, shape):
+    """With FR_WEIGHTS_IN_WORKSPACE the adjoint and a second accumulation read
+    the fractions the forward left in the caller's workspace: results equal
+    bit for bit those that recompute them."""
+    ny, nx = shape
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=nx + 7)
+    rain = inputs.rain_field(ny, nx, 3)
+    zt, rt = cuda(z), cuda(rain)
+    ws = torch.empty(api.workspace_size(nx, ny, mfd=True), dtype=torch.uint8, device="cuda")
+    fused = api.route_mfd(zt, 30.0, 1.1, rt, want_lo=True, want_mask=True, ws=ws)
+    Rk = api.routing_mfd(fused["mask"], zt, 30.0, 1.1, _lib.FR_WEIGHTS_IN_WORKSPACE)
+    kept = api.adjoint(Rk, fused["w"], fused["w_lo"], want_dz=True, ws=ws)
+    R = api.routing_mfd(fused["mask"], zt, 30.0, 1.1)
+    ref = api.adjoint(R, fused["w"], fused["w_lo"], want_dz=True)
+    assert torch.equal(kept[0], ref[0]) and torch.equal(kept[1], ref[1])
+    # the adjoint left the fractions in place: an accumulation may reuse them
+    again = api.accumulate(Rk, rt, want_w=True, want_lo=True, ws=ws)
+    assert torch.equal(again["w"], fused["w"]) and torch.equal(again["w_lo"], fused["w_lo"])
+    assert api.get_status(ws=ws) == 0 and api.get_status() == 0
+
+
+def test_autograd_route_mfd_keep_weights(api):
+    """RouteMFD with the forward's fractions kept gives the gradients of the
+    default (recomputing) backward bit for bit."""
+    ny, nx = 70, 90
+    z = inputs.fractal_dem(ny, nx, beta=2.2, tilt=0.0, seed=11)
+    rain = inputs.rain_field(ny, nx, 11)
+    gbar = cuda(np.random.default_rng(4).random((ny, nx)).astype(np.float32))
+    grads = []
+    for keep in (False, True):
+        zt = cuda(z).requires_grad_(True)
+        rt = cuda(rain).requires_grad_(True)
+        w = api.RouteMFD.apply(zt, rt, 30.0, 1.1, 0, keep)
+        (w * gbar).sum().backward()
+        grads.append((zt.grad, rt.grad))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
 
 
 def test_autograd_route_mfd(api):
