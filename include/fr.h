@@ -111,6 +111,22 @@ typedef enum {
  *                  library cannot check this; wrong fractions give wrong
  *                  results, not an error.  D8 routings and the receiver,
  *                  fused route and batch calls reject this flag.
+ * Routing flag of D8 routings, for fr_mass_balance: the area term formed where
+ * the areas are produced.  An accumulation with areas sums the areas of the
+ * FR_SINK cells its local phase finishes into the workspace and marks the
+ * cells it leaves to its global phase there.
+ *   FR_SINK_SUMS_IN_WORKSPACE  the workspace holds these records of the
+ *                  accumulation that wrote `area` for this routing (the last
+ *                  fr_accumulate or fr_route_d8 with areas on the workspace).
+ *                  fr_mass_balance then takes the area term from them and
+ *                  reads `area` only at the FR_SINK cells among the global
+ *                  cells, instead of at every FR_SINK cell; the result is the
+ *                  same.  It needs `area` and no `w`; with `rain` the rain
+ *                  term is still summed over the field.  fr_accumulate and
+ *                  fr_route_adjoint ignore the flag; MFD routings and the
+ *                  receiver, fused route and batch calls reject it.  As with
+ *                  FR_WEIGHTS_IN_WORKSPACE, the library cannot check the
+ *                  claim.
  */
 #define FR_EDGE_SINK 0x0u
 #define FR_EDGE_ROUTE 0x1u
@@ -122,6 +138,7 @@ typedef enum {
 #define FR_GLOBAL_WALKERS 0x20u
 #define FR_GLOBAL_SKELETON 0x40u
 #define FR_WEIGHTS_IN_WORKSPACE 0x80u
+#define FR_SINK_SUMS_IN_WORKSPACE 0x100u
 
 #define FR_SINK 0xFFu
 
@@ -342,8 +359,11 @@ fr_status fr_route_adjoint(const fr_routing* routing, const float* w, const floa
  *   out_dev[0] = sum over sinks of (w + w_lo)   (0 if w is NULL)
  *   out_dev[1] = sum of rain (nx*ny for unit rain)
  *   out_dev[2] = sum over sinks of area         (0 if area is NULL), exact
+ * Sinks are the cells whose routing byte is FR_SINK (D8) or 0 (MFD).
  * The reduction order is fixed, so repeated calls give identical bits.
- * Workspace: fr_workspace_size(FR_OP_MASS_BALANCE, nx, ny, flags).
+ * Workspace: fr_workspace_size(FR_OP_MASS_BALANCE, nx, ny, flags).  With
+ * FR_SINK_SUMS_IN_WORKSPACE (D8 routings; w NULL, area given) the area term
+ * comes from the records the accumulation left in the same workspace.
  */
 fr_status fr_mass_balance(const fr_routing* routing, const float* rain, const float* w,
                           const float* w_lo, const uint64_t* area, double* out_dev, void* ws,

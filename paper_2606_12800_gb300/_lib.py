@@ -33,6 +33,7 @@ FR_DINF = 0x10
 FR_GLOBAL_WALKERS = 0x20
 FR_GLOBAL_SKELETON = 0x40
 FR_WEIGHTS_IN_WORKSPACE = 0x80
+FR_SINK_SUMS_IN_WORKSPACE = 0x100
 FR_CHECK_FINITE = 0x4
 FR_SINK = 0xFF
 

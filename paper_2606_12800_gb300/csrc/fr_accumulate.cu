@@ -95,6 +95,62 @@ __global__ void __launch_bounds__(MB_NT) k_mass_partial(int64_t n, const uint8_t
     }
 }
 
+// Area term of the D8 mass balance from the sums an accumulation left in the
+// workspace: the local phase's sum over the FR_SINK cells it finished plus,
+// gathered here, the areas of the FR_SINK cells among the global cells (set
+// bits of the global-cell bitmap).  Each cell is finished by exactly one of
+// the two phases, so the total equals the sum over all FR_SINK cells.  Block b
+// writes the area term of partials[3 b + 2]; with `unit` (no rain field) it
+// also writes the other two terms (0, and the cell count in block 0), which
+// k_mass_partial has written otherwise.
+__global__ void __launch_bounds__(MB_NT) k_mass_sinks_ws(int64_t n, const uint8_t* __restrict__ rb,
+                                                         const uint64_t* __restrict__ area,
+                                                         const uint32_t* __restrict__ gbits,
+                                                         const EngineGlobals* __restrict__ G,
+                                                         bool unit, double* __restrict__ partials) {
+    unsigned long long sa = 0;
+    auto take = [&](int64_t wd, uint32_t m) {  // the set bits of bitmap word wd
+        for (; m; m &= m - 1) {
+            const int64_t i = 32 * wd + (__ffs(m) - 1);
+            if (i < n && __ldg(rb + i) == kSink) sa += __ldg(area + i);
+        }
+    };
+    // the bitmap in 16-byte groups of four words, four groups in flight per
+    // thread (the bitmap is 256-byte aligned in the workspace)
+    const int64_t words = (n + 31) / 32, quads = words / 4;
+    const int64_t stride = (int64_t)gridDim.x * MB_NT, first = (int64_t)blockIdx.x * MB_NT + threadIdx.x;
+    const uint4* g4 = reinterpret_cast<const uint4*>(gbits);
+    for (int64_t q0 = first; q0 < quads; q0 += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = q0 + u * stride < quads ? __ldg(g4 + q0 + u * stride) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!(v[u].x | v[u].y | v[u].z | v[u].w)) continue;
+            const int64_t wd = 4 * (q0 + u * stride);
+            take(wd, v[u].x);
+            take(wd + 1, v[u].y);
+            take(wd + 2, v[u].z);
+            take(wd + 3, v[u].w);
+        }
+    }
+    for (int64_t wd = 4 * quads + first; wd < words; wd += stride) take(wd, __ldg(gbits + wd));
+    for (int o = 16; o; o >>= 1) sa += __shfl_down_sync(0xffffffffu, sa, o);
+    __shared__ unsigned long long s2[MB_NT / 32];
+    if ((threadIdx.x & 31) == 0) s2[threadIdx.x >> 5] = sa;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c = blockIdx.x == 0 ? G->sink_area : 0ull;
+        for (int i = 0; i < MB_NT / 32; ++i) c += s2[i];
+        reinterpret_cast<unsigned long long*>(partials)[3 * blockIdx.x + 2] = c;
+        if (unit) {
+            partials[3 * blockIdx.x + 0] = 0.0;
+            partials[3 * blockIdx.x + 1] = blockIdx.x == 0 ? (double)n : 0.0;
+        }
+    }
+}
+
 __global__ void k_mass_final(const double* __restrict__ partials, int nblocks, double* out) {
     __shared__ double s0[256], s1[256];
     __shared__ unsigned long long s2[256];
@@ -241,6 +297,22 @@ cudaError_t launch_mfd_grad_z(const Prob& P, const float* g_hi, const float* g_l
                               cudaStream_t s) {
     const int64_t tiles = ((P.nx + GTX - 1) / GTX) * ((P.ny + GTY - 1) / GTY);
     k_mfd_grad_z<<<(unsigned)tiles, GNT, 0, s>>>(P, g_hi, g_lo, dLdz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_balance_ws(int64_t nx, int64_t ny, const uint8_t* rb, const float* rain,
+                                   const uint64_t* area, const uint32_t* gbits,
+                                   const EngineGlobals* G, double* partials, int nblocks,
+                                   double* out, cudaStream_t s) {
+    const int64_t n = nx * ny;
+    cudaError_t e;
+    if (rain) {  // the rain sum as in the full pass; its area term is replaced below
+        k_mass_partial<false><<<nblocks, MB_NT, 0, s>>>(n, rb, rain, nullptr, nullptr, nullptr, partials);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_mass_sinks_ws<<<nblocks, MB_NT, 0, s>>>(n, rb, area, gbits, G, rain == nullptr, partials);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_mass_final<<<1, 256, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
 }
 

@@ -16,10 +16,11 @@ namespace {
 constexpr int64_t kMaxCells = (int64_t)1 << 40;
 constexpr int kMassBlocks = 1024;
 constexpr uint32_t kKnownFlags = FR_EDGE_ROUTE | FR_D8_LOWEST | FR_CHECK_FINITE | FR_D4 | FR_DINF |
-                                 FR_GLOBAL_WALKERS | FR_GLOBAL_SKELETON | FR_WEIGHTS_IN_WORKSPACE;
-// flags of the receiver and fused route calls: the weights flag describes a
-// routing's workspace and has no meaning there
-constexpr uint32_t kCallFlags = kKnownFlags & ~FR_WEIGHTS_IN_WORKSPACE;
+                                 FR_GLOBAL_WALKERS | FR_GLOBAL_SKELETON | FR_WEIGHTS_IN_WORKSPACE |
+                                 FR_SINK_SUMS_IN_WORKSPACE;
+// flags of the receiver and fused route calls: the workspace flags describe a
+// routing's workspace and have no meaning there
+constexpr uint32_t kCallFlags = kKnownFlags & ~(FR_WEIGHTS_IN_WORKSPACE | FR_SINK_SUMS_IN_WORKSPACE);
 
 // D8 forward: the global phase switches from the cell walkers to the
 // tile-skeleton solve when the local phase leaves at least this share of the
@@ -116,6 +117,7 @@ bool routing_ok(const fr_routing* R) {
     if (R->kind == FR_ROUTING_MFD)
         return R->mask && R->dem && std::isfinite(R->dx) && R->dx > 0 && std::isfinite(R->p) &&
                R->p > 0 && R->p <= FR_MFD_MAX_P && (R->flags & ~kKnownFlags) == 0 &&
+               !(R->flags & FR_SINK_SUMS_IN_WORKSPACE) &&
                !(R->flags & FR_D4);
     return false;
 }
@@ -479,12 +481,19 @@ fr_status fr_mass_balance(const fr_routing* R, const float* rain, const float* w
                           size_t ws_bytes, void* stream) {
     if (!routing_ok(R) || !out_dev) return FR_ERR_INVALID_ARG;
     if (w_lo && !w) return FR_ERR_INVALID_ARG;
+    const bool sums = R->flags & FR_SINK_SUMS_IN_WORKSPACE;  // D8 only (routing_ok)
+    if (sums && (w || !area)) return FR_ERR_INVALID_ARG;
     const int64_t n = R->nx * R->ny;
     if (!ws_ok(ws, ws_bytes, n)) return FR_ERR_WORKSPACE;
     const Layout L = layout(n);
     int64_t blocks = (n + 255) / 256;
     if (blocks > kMassBlocks) blocks = kMassBlocks;
     const uint8_t* rb = R->kind == FR_ROUTING_D8 ? R->dir : R->mask;
+    if (sums)
+        return cuda_status(launch_mass_balance_ws(
+            R->nx, R->ny, rb, rain, area, reinterpret_cast<const uint32_t*>((char*)ws + L.gbits),
+            reinterpret_cast<const EngineGlobals*>(ws), reinterpret_cast<double*>((char*)ws + L.partials),
+            (int)blocks, out_dev, (cudaStream_t)stream));
     return cuda_status(launch_mass_balance(R->kind, R->nx, R->ny, rb, rain, w, w_lo, area,
                                            reinterpret_cast<double*>((char*)ws + L.partials),
                                            (int)blocks, out_dev, (cudaStream_t)stream));

@@ -60,6 +60,9 @@ struct D8Geo {
 // than 2^16 cells).  Donors in the ring around the region never arrive, so a
 // cell with upstream water outside the region never becomes final.
 constexpr uint32_t kPkArrive = 1u << 20, kPkArea = 0xFFFFu, kPkDone = 9u;
+// Shared code of a cell without a receiver in the grid whose routing byte is
+// not FR_SINK (an invalid code, or one pointing out of the grid).
+constexpr uint8_t kNoRecv = 0xFE;
 __device__ __forceinline__ bool pk_final(uint32_t pk) { return (pk >> 20) == kPkDone; }
 
 // Shared memory of one tile; per-cell arrays use the ring layout of `code`
@@ -77,7 +80,8 @@ struct SmemD8 {
     int qtail;                                    // its length
     int head;                                     // next entry to hand out
     int nglob;                                    // unfinished inner cells listed in queue after the walk
-    unsigned long long done, gbase;
+    unsigned long long gbase;
+    unsigned int done, sinks;  // block sums of the publish step (at most 2^16 and NE)
 };
 
 // Warp-aggregated append of four optional cells per lane (-1: none; all lanes
@@ -338,16 +342,19 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
         }
     } else {
         // ---- scalar path (tiles touching the grid boundary)
+        // codes without a receiver in the grid become kNoRecv unless they are
+        // FR_SINK, so that kSink marks exactly the routing bytes FR_SINK (the
+        // mass balance's sinks), as on the vector path, which keeps the bytes
         for (int i = tid; i < RY * CP; i += NT8) {
             const int ry = i / CP, rx = i - ry * CP - 3;
-            uint8_t code = kSink;
+            uint8_t code = kNoRecv;
             if (rx >= gx_lo && rx < gx_hi && ry >= gy_lo && ry < gy_hi) {
                 code = rd_rb(P, (oy + ry) * P.nx + (ox + rx));
                 if (code < 8) {
                     const int xr = rx + offx(code), yr = ry + offy(code);
-                    if (xr < gx_lo || xr >= gx_hi || yr < gy_lo || yr >= gy_hi) code = kSink;
-                } else {
-                    code = kSink;
+                    if (xr < gx_lo || xr >= gx_hi || yr < gy_lo || yr >= gy_hi) code = kNoRecv;
+                } else if (code != kSink) {
+                    code = kNoRecv;
                 }
             }
             S.code[i] = code;
@@ -460,8 +467,14 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
 
     // ---- inner tile: publish final cells; a cell that did not finish has
     // upstream water outside the extended region (or lies on a cycle) and is
-    // listed as global
-    unsigned long long done = 0;
+    // listed as global.  With areas, the areas of the finished cells whose
+    // routing byte is FR_SINK are summed for the mass balance (the global
+    // phase's cells are summed there from the global-cell bits).
+    // Per-thread counts: at most 16 inner cells a thread, areas below 2^16.
+    // Whole vector tiles count their finished cells as the inner cells less the
+    // listed ones instead.
+    uint32_t done = 0, sinks = 0;
+    const bool whole = vec && x0 + TX <= P.nx && y0 + TY <= P.ny;
     auto need_lo_of = [&](int r, int lx, int ly) -> bool {
         // a cell's trailing word is pulled later when its receiver leaves the
         // inner tile (another tile may list it as global) or is global here
@@ -489,8 +502,10 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
             if (P.lo_full || need_lo_of(r, lx, ly)) wr_f(P.out_lo, P, gi, S.vlo[r], 28);
         }
         if constexpr (AREA) wr_area(P, gi, 1u + (pkc & kPkArea));
+        if constexpr (AREA && !BATCH)
+            if (S.code[r] == kSink) sinks += 1u + (pkc & kPkArea);
     };
-    if (vec && x0 + TX <= P.nx && y0 + TY <= P.ny) {
+    if (whole) {
         for (int gq = tid; gq < TX * TY / 4; gq += NT8) {
             const int ly = gq / (TX / 4), lx = (gq - ly * (TX / 4)) * 4;
             const int r = (ly + H + 1) * CP + lx + H + 4;
@@ -500,7 +515,6 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
                 for (int q = 0; q < 4; ++q) publish_one(lx + q, ly);  // rare: global cells
                 continue;
             }
-            done += 4;
             const int64_t gi = (y0 + ly) * P.nx + x0 + lx;
             if constexpr (W) {
                 *reinterpret_cast<float4*>(P.out_hi + gi) = *reinterpret_cast<const float4*>(S.vhi + r);
@@ -513,6 +527,14 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
                 ulonglong2* out = reinterpret_cast<ulonglong2*>(P.area + gi);
                 out[0] = make_ulonglong2(1u + (p4.x & kPkArea), 1u + (p4.y & kPkArea));
                 out[1] = make_ulonglong2(1u + (p4.z & kPkArea), 1u + (p4.w & kPkArea));
+                if constexpr (!BATCH) {
+                    // byte q of sk is 1 where routing byte q is FR_SINK; the areas
+                    // are 1 + the 16-bit donor sums: a count plus two 16x8-bit dot
+                    // products over the packed sums
+                    const uint32_t sk = zero_bytes(~*reinterpret_cast<const uint32_t*>(S.code + r)) >> 7;
+                    sinks += __popc(sk) + __dp2a_lo(__byte_perm(p4.x, p4.y, 0x5410), sk, 0u) +
+                             __dp2a_hi(__byte_perm(p4.z, p4.w, 0x5410), sk, 0u);
+                }
             }
         }
     } else {
@@ -521,12 +543,23 @@ __global__ void __launch_bounds__(Gm::NT) k_local_d8(Prob Pone, EngineGlobals* G
             publish_one(lx, ly);
         }
     }
-    for (int o = 16; o; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);
-    if (tid == 0) S.done = 0;
+    // warp sums fit 32 bits (512 cells; areas of disjoint basins, below NE)
+    const uint32_t done_w = whole ? 0u : __reduce_add_sync(0xffffffffu, done);
+    uint32_t sinks_w = 0;
+    if constexpr (AREA && !BATCH) sinks_w = __reduce_add_sync(0xffffffffu, sinks);
+    if (tid == 0) {
+        S.done = 0;
+        S.sinks = 0;
+    }
     __syncthreads();
-    if ((tid & 31) == 0 && done) atomicAdd(&S.done, done);
+    if ((tid & 31) == 0 && done_w) atomicAdd(&S.done, done_w);
+    if (AREA && !BATCH && (tid & 31) == 0 && sinks_w) atomicAdd(&S.sinks, sinks_w);
     __syncthreads();
-    if (tid == 0 && S.done) atomicAdd(&G->done_cells, S.done);
+    if (tid == 0) {
+        const unsigned long long d = whole ? (unsigned long long)(TX * TY - S.nglob) : S.done;
+        if (d) atomicAdd(&G->done_cells, d);
+        if (AREA && !BATCH && S.sinks) atomicAdd(&G->sink_area, (unsigned long long)S.sinks);
+    }
     if (S.nglob) list_global(S, P, G, pid, TX, x0, y0, NT8);
 }
 

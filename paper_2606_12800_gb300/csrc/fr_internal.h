@@ -65,7 +65,8 @@ struct EngineGlobals {
     unsigned int bar_gen;            // grid barrier: generation
     unsigned long long rounds;       // level-synchronous global phase: rounds run (diagnostic)
     unsigned long long skel_tiles;   // skeleton solve: tiles listed in Prob::sktiles
-    unsigned long long pad[3];
+    unsigned long long sink_area;    // D8 areas: sum of the areas of the FR_SINK cells the local phase finished
+    unsigned long long pad[2];
 };
 static_assert(sizeof(EngineGlobals) == 128, "globals block is 128 bytes (256 reserved)");
 
@@ -118,6 +119,13 @@ cudaError_t launch_mass_balance(int kind, int64_t nx, int64_t ny, const uint8_t*
                                 const float* rain, const float* w, const float* w_lo,
                                 const uint64_t* area, double* partials, int nblocks,
                                 double* out, cudaStream_t s);
+// D8 areas (fr_mass_balance with FR_SINK_SUMS_IN_WORKSPACE): the area term from
+// the local phase's sink sum and the global cells' sinks, the rain term from
+// `rain` (a full pass) or the cell count.
+cudaError_t launch_mass_balance_ws(int64_t nx, int64_t ny, const uint8_t* rb, const float* rain,
+                                   const uint64_t* area, const uint32_t* gbits,
+                                   const EngineGlobals* G, double* partials, int nblocks,
+                                   double* out, cudaStream_t s);
 // Richardson I+X (fr_richardson.cu): one sweep prev -> next over 64x32
 // subdomains (counts[0] += changed cells, counts[1] += finalised cells), and
 // the copy of converged two-float values into the outputs.

@@ -42,7 +42,7 @@ def test_workspace_size(lib):
     assert n >= 4096 * 4096 * 13
     assert n % 256 == 0
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 0, 10, 0) == 0
-    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 10, 10, 0x100) == 0  # an unknown flag
+    assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 10, 10, 0x200) == 0  # an unknown flag
     assert lib.fr_workspace_size(_lib.FR_OP_ACCUMULATE, 1 << 21, 1 << 21, 0) == 0  # > 2^40 cells
     # MFD operations keep 8 fp32 fractions per cell on top of the common part
     m = lib.fr_workspace_size(_lib.FR_OP_MFD, 4096, 4096, 0)
@@ -152,3 +152,28 @@ def test_weights_flag_only_for_mfd_routings(lib):
                            None) == _lib.FR_ERR_INVALID_ARG
     assert lib.fr_route_mfd(fake, 8, 8, 30.0, 1.1, W, None, fake, None, None, fake, 1 << 20,
                             None) == _lib.FR_ERR_INVALID_ARG
+
+
+def test_sink_sums_flag_only_for_d8_routings(lib):
+    """FR_SINK_SUMS_IN_WORKSPACE describes a D8 accumulation's workspace: MFD
+    routings, the receiver calls and the fused routes reject it, and the
+    mass balance with it needs areas and no water."""
+    fake = ctypes.c_void_p(0x1000)
+    S = _lib.FR_SINK_SUMS_IN_WORKSPACE
+    R = _lib.fr_routing()
+    R.kind, R.nx, R.ny, R.mask, R.dem, R.dx, R.p, R.flags = \
+        _lib.FR_ROUTING_MFD, 8, 8, 0x1000, 0x2000, 30.0, 1.1, S
+    ws = 1 << 22
+    assert lib.fr_accumulate(ctypes.byref(R), None, fake, None, None, fake, ws, None) == \
+        _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_mass_balance(ctypes.byref(R), None, None, None, fake, fake, fake, ws, None) == \
+        _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_receivers_d8(fake, 8, 8, 30.0, S, fake, None, None) == _lib.FR_ERR_INVALID_ARG
+    assert lib.fr_route_d8(fake, 8, 8, 30.0, S, None, fake, None, None, None, fake, ws,
+                           None) == _lib.FR_ERR_INVALID_ARG
+    D = _lib.fr_routing()
+    D.kind, D.nx, D.ny, D.dir, D.flags = _lib.FR_ROUTING_D8, 8, 8, 0x1000, S
+    assert lib.fr_mass_balance(ctypes.byref(D), None, fake, None, fake, fake, fake, ws, None) == \
+        _lib.FR_ERR_INVALID_ARG  # water
+    assert lib.fr_mass_balance(ctypes.byref(D), None, None, None, None, fake, fake, ws, None) == \
+        _lib.FR_ERR_INVALID_ARG  # no areas

@@ -257,6 +257,66 @@ def test_mass_balance(api):
     assert np.array_equal(mb, mb2)
 
 
+def _sink_sum_dem(kind, ny, nx, api):
+    if kind == "plane":
+        x = np.arange(nx, dtype=np.float64)[None, :]
+        y = np.arange(ny, dtype=np.float64)[:, None]
+        return cuda(np.ascontiguousarray((1000.0 - x - 0.37 * y).astype(np.float32)))
+    zt = cuda(inputs.fractal_dem(ny, nx, beta=2.0, tilt=0.01, seed=nx + ny))
+    if kind == "filled":
+        zt = api.fill(zt)[0]
+    return zt
+
+
+@pytest.mark.parametrize("kind,shape", [("rough", (1, 9)), ("rough", (3, 3)), ("rough", (300, 517)),
+                                        ("rough", (704, 1024)), ("filled", (600, 640)),
+                                        ("plane", (256, 384))])
+@pytest.mark.parametrize("gflags", [0, _lib.FR_GLOBAL_WALKERS, _lib.FR_GLOBAL_SKELETON])
+def test_mass_balance_sink_sums(api, kind, shape, gflags):
+    """FR_SINK_SUMS_IN_WORKSPACE: the area term from the accumulation's sums
+    (local phase) and the global cells' sinks equals the full pass over the
+    stored areas bit for bit, through the cell walkers and the skeleton
+    solve, with and without a rain field."""
+    ny, nx = shape
+    zt = _sink_sum_dem(kind, ny, nx, api)
+    d = api.receivers_d8(zt)
+    Rs = api.routing_d8(d, gflags | _lib.FR_SINK_SUMS_IN_WORKSPACE)
+    area = api.accumulate(Rs, None, want_w=False, want_area=True)["area"]
+    fused = api.mass_balance(Rs, area=area).cpu().numpy()
+    full = api.mass_balance(api.routing_d8(d, gflags), area=area).cpu().numpy()
+    assert fused.tobytes() == full.tobytes()
+    assert fused[2] == nx * ny and fused[1] == nx * ny and fused[0] == 0.0
+    rt = cuda(inputs.rain_field(ny, nx, 5))
+    fused_r = api.mass_balance(Rs, rain=rt, area=area).cpu().numpy()
+    full_r = api.mass_balance(api.routing_d8(d, gflags), rain=rt, area=area).cpu().numpy()
+    assert fused_r.tobytes() == full_r.tobytes()
+    assert api.get_status() == 0
+
+
+def test_mass_balance_sink_sums_count_only_sink_codes(api):
+    """Codes pointing out of the grid act as no receiver in the accumulation
+    but are not FR_SINK: both forms of the mass balance leave them out."""
+    ny, nx = 300, 400
+    z = cuda(inputs.fractal_dem(ny, nx, beta=2.0, tilt=0.01, seed=9))
+    d = api.receivers_d8(z)
+    d[0, 5:300] = 1     # N from the top row: out of the grid
+    d[100:200, 0] = 2   # W from the left column
+    Rs = api.routing_d8(d, _lib.FR_SINK_SUMS_IN_WORKSPACE)
+    area = api.accumulate(Rs, None, want_w=False, want_area=True)["area"]
+    fused = api.mass_balance(Rs, area=area).cpu().numpy()
+    full = api.mass_balance(api.routing_d8(d), area=area).cpu().numpy()
+    assert fused.tobytes() == full.tobytes()
+    a = area.cpu().numpy()
+    assert fused[2] == nx * ny - a[0, 5:300].sum() - a[100:200, 0].sum()
+    # the flag needs areas and no water
+    w = api.accumulate(Rs, None, want_w=True, want_area=True)
+    with pytest.raises(RuntimeError):
+        api.mass_balance(Rs, w=w["w"], area=w["area"])
+    with pytest.raises(RuntimeError):
+        api.mass_balance(Rs)
+    assert api.get_status() == 0
+
+
 def test_cycle_reports_no_progress(api):
     """A routing with a cycle (two cells pointing at each other) must finish
     and leave FR_ERR_NO_PROGRESS in the status word (no hang)."""
