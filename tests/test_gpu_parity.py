@@ -52,7 +52,7 @@ def test_receivers_d8_bit_exact(api, shape, flags):
     np.testing.assert_array_equal(n.cpu().numpy(), oracle.indegree(d_ref, False))
 
 
-TMA_SHAPES = [(32, 128), (33, 132), (129, 260), (31, 1028), (1000, 1028), (4097, 8), (8, 4096),
+TMA_SHAPES = [(64, 128), (65, 132), (129, 260), (31, 1028), (1000, 1028), (4097, 8), (8, 4096),
               (513, 640)]
 
 
