@@ -373,27 +373,37 @@ def main():
         zc = np.ascontiguousarray(z[:D8_CROP, :D8_CROP].cpu().numpy())
         cpu, crop = d8_crop_check(api, zc)
 
-    # end to end through the public API: pinned host DEM in, areas and the
-    # mass balance back to pinned host memory, copies timed
+    # end to end through the public API: the DEM from pinned host memory to
+    # the device, fr_route_d8 and the mass balance there, the areas, the codes
+    # and the mass balance back into pinned host buffers; copies timed
     z_host = z.cpu().pin_memory()
     del z, dir_, area
     torch.cuda.empty_cache()
+    area_h = torch.empty((n, n), dtype=torch.int64, pin_memory=True)
+    dir_h = torch.empty((n, n), dtype=torch.uint8, pin_memory=True)
+    mb_h = torch.empty(3, dtype=torch.float64, pin_memory=True)
     e2e_ms = []
     for i in range(max(3, min(K, 5)) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = api.route_d8(z_host, DX, None, 0, want_w=False, want_area=True, want_dir=True)
-        Rh = api.routing_d8(out["dir"].to(dev, non_blocking=True), _lib.FR_SINK_SUMS_IN_WORKSPACE)
-        m = api.mass_balance(Rh, area=out["area"].to(dev, non_blocking=True), device=dev).cpu()
+        zd = z_host.to(dev, non_blocking=True)
+        out = api.route_d8(zd, DX, None, 0, want_w=False, want_area=True, want_dir=True)
+        Rh = api.routing_d8(out["dir"], _lib.FR_SINK_SUMS_IN_WORKSPACE)
+        m = api.mass_balance(Rh, area=out["area"], device=dev)
+        area_h.copy_(out["area"], non_blocking=True)
+        dir_h.copy_(out["dir"], non_blocking=True)
+        mb_h.copy_(m, non_blocking=True)
         torch.cuda.synchronize()
         if i >= 1:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        del out, Rh, m
+        del zd, out, Rh, m
+    assert mb_h[2].item() == cells and mb_h[1].item() == cells, mb_h
     e2e = {"value": cells / (statistics.median(e2e_ms) * 1e-3), "unit": "cells/s",
            "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": cells * 9 + 24,
            "ms_per_step": statistics.median(e2e_ms),
-           "path": "api.route_d8 (fr_route_d8) from pinned host DEM; areas + codes to host"}
-    del z_host
+           "path": "pinned host DEM to the device, api.route_d8 (fr_route_d8) and api.mass_balance "
+                   "there, areas + codes + mass balance into pinned host buffers"}
+    del z_host, area_h, dir_h, mb_h
     torch.cuda.empty_cache()
 
     extra = {}
