@@ -4,7 +4,9 @@ chosen size (``ncu -k ...  python -m paper_2606_12800_gb300.cases mfd --n 4096``
 Cases (all on seeded synthetic fractal DEMs, inputs resident on the device):
   d8        receivers + D8 accumulation with rain U[0,1) (two-float w, uint64 areas)
   d8_area   receivers + D8 unit-rain areas only
-  d8_step   receivers + D8 unit-rain areas + the mass balance (the benchmark step)
+  d8_step   receivers + D8 unit-rain areas + the mass balance as a full pass over
+            the stored areas (the benchmark step takes the mass balance's area term
+            from the accumulation's sink sums instead)
   mfd       slope-split route (p = 1.1), unit rain
   adjoint   slope-split route, then the adjoint of L = sum over sinks of w^2
             (dL/drain and dL/dz)
