@@ -116,17 +116,18 @@ typedef enum {
  * FR_SINK cells its local phase finishes into the workspace and marks the
  * cells it leaves to its global phase there.
  *   FR_SINK_SUMS_IN_WORKSPACE  the workspace holds these records of the
- *                  accumulation that wrote `area` for this routing (the last
- *                  fr_accumulate or fr_route_d8 with areas on the workspace).
- *                  fr_mass_balance then takes the area term from them and
- *                  reads `area` only at the FR_SINK cells among the global
- *                  cells, instead of at every FR_SINK cell; the result is the
- *                  same.  It needs `area` and no `w`; with `rain` the rain
- *                  term is still summed over the field.  fr_accumulate and
- *                  fr_route_adjoint ignore the flag; MFD routings and the
- *                  receiver, fused route and batch calls reject it.  As with
- *                  FR_WEIGHTS_IN_WORKSPACE, the library cannot check the
- *                  claim.
+ *                  accumulation that wrote `area` for this routing: that
+ *                  fr_accumulate or fr_route_d8 call (with areas) was the
+ *                  last call on the workspace other than fr_mass_balance and
+ *                  fr_get_status.  fr_mass_balance then takes the area term
+ *                  from them and reads `area` only at the FR_SINK cells among
+ *                  the global cells, instead of at every FR_SINK cell; the
+ *                  result is the same.  It needs `area` and no `w`; with
+ *                  `rain` the rain term is still summed over the field.
+ *                  fr_accumulate and fr_route_adjoint ignore the flag; MFD
+ *                  routings and the receiver, fused route and batch calls
+ *                  reject it.  As with FR_WEIGHTS_IN_WORKSPACE, the library
+ *                  cannot check the claim.
  */
 #define FR_EDGE_SINK 0x0u
 #define FR_EDGE_ROUTE 0x1u
