@@ -509,7 +509,8 @@ bool encode_tile_map_f32(CUtensorMap* map, const float* base, int64_t nx, int64_
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    // the driver's entry point, looked up once (thread-safe static initialisation)
+    // cuTensorMapEncodeTiled from the CUDA driver API, looked up once (thread-safe static
+    // initialisation)
     static const Encode fn = []() -> Encode {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
