@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(RNT) k_receivers_d8(const float* __restrict__ 
 // ---------------------------------------------------------------- TMA path
 // D8 codes without donor counts, by a persistent kernel: each CTA walks its
 // tiles of TTX x TTY cells, the elevations of a tile plus a one-cell halo
-// arriving by TMA into one of NS shared-memory stages while the previous tiles
+// arriving by TMA into one of TNS shared-memory stages while the previous tiles
 // are computed.  The box starts 4 cells left of the tile (its x coordinate a
 // multiple of 4, as TMA requires), so it is TTX + 8 wide.  The kernel is bound
 // by the ALU pipe (the compare-and-select chain of eight directions per cell);
